@@ -1,0 +1,110 @@
+"""Pins of the oracle's spiking-network compositions (CPU only).
+
+The plaintext DiCSNN is pinned by a hand-worked LIF trace (Thm 3.2); the
+encrypted DiCSNN is pinned to the plaintext network spike for spike on the
+low-noise test set (4.2 FHE-Fire / FHE-Reset, Thm 4.1 respected).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2309_09025_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _traces():
+    out = []
+    for line in open(os.path.join(GOLDEN, "lif_trace.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        parts = [p.split() for p in line.split("|")]
+        v_th, leak = int(parts[0][0]), int(parts[0][1])
+        I, H, S, V = ([int(x) for x in p] for p in parts[1:])
+        out.append((v_th, leak, I, H, S, V))
+    return out
+
+
+@pytest.mark.parametrize("trace", _traces())
+def test_plain_lif_matches_hand_worked_trace(trace):
+    v_th, leak, I, H, S, V = trace
+    P = dict(synth.P64)  # p = 32: every value of the trace is in [-16, 16)
+    net = {"layers": [{"type": "fc", "W": np.array([[1]], np.int32)}],
+           "lif": dict(v_th=v_th, leak_shift=leak, spike_scale=1), "T": len(I),
+           "static_input": False}
+    res = O.snn_plain(P, net, np.array(I, np.int64).reshape(-1, 1))
+    assert res["h"][0][:, 0].tolist() == H
+    assert res["spikes"][0][:, 0].tolist() == S
+    assert int(res["scores"][0]) == sum(S)
+    # V trace: V[t] = Reset(H[t]) is what the next step adds to I[t+1]
+    assert [H[t + 1] - I[t + 1] for t in range(len(I) - 1)] == V[:-1]
+
+
+def test_lif_luts_follow_fhe_fire_and_reset():
+    """Eq. FHE-Fire: 2*Spike = Sign(m)+1 style step at V_th; Eq. FHE-Reset:
+    0 above threshold, leak in [0, V_th), 0 below 0 -- on the centred input."""
+    P = dict(synth.P630)
+    p = 1 << P["log2_p"]
+    fire, reset = O.lif_luts(P, v_th=8, leak_shift=1, spike_scale=2)
+    v = np.arange(p) - p // 2
+    assert np.array_equal(fire[v >= 8], np.full((v >= 8).sum(), 2))
+    assert np.all(fire[v < 8] == 0)
+    assert np.all(reset[v >= 8] == 0) and np.all(reset[v < 0] == 0)
+    mid = (v >= 0) & (v < 8)
+    assert reset[mid].tolist() == [0, 0, 1, 1, 2, 2, 3, 3]
+
+
+def _small_net(seed, T=3):
+    g = np.random.default_rng(seed)
+    W1 = g.integers(-1, 2, (5, 6)).astype(np.int32)
+    W2 = g.integers(-1, 2, (3, 5)).astype(np.int32)
+    return {"layers": [{"type": "fc", "W": W1}, {"type": "fc", "W": W2}],
+            "lif": dict(v_th=2, leak_shift=1, spike_scale=1), "T": T,
+            "static_input": False}
+
+
+def test_thm41_invariant_plain():
+    """Thm 4.1: if V_th + max|I| <= p/2 then H in [V_th - p/2, p/2)."""
+    P = dict(synth.T0)
+    p = 1 << P["log2_p"]
+    net = _small_net(3, T=6)
+    x = synth.bernoulli_spikes(4, 6, 6, 0.5)
+    res = O.snn_plain(P, net, x)
+    for li, layer in enumerate(net["layers"]):
+        max_I = np.abs(layer["W"]).sum(axis=1).max()
+        assert net["lif"]["v_th"] + max_I <= p // 2
+        H = res["h"][li]
+        assert H.min() >= net["lif"]["v_th"] - p // 2 and H.max() < p // 2
+
+
+def test_encrypted_snn_matches_plain(oracle_keys):
+    """Encrypted DiCSNN = plaintext DiCSNN spike for spike on the low-noise
+    set (bootstraps never fail there), including the spike-count scores."""
+    P, K = oracle_keys("T0", 31)
+    net = _small_net(5, T=3)
+    x = synth.bernoulli_spikes(6, 3, 6, 0.5)
+    plain = O.snn_plain(P, net, x)
+    ct = O.encrypt(P, K, x.reshape(-1), 77).reshape(3, 6, -1)
+    enc = O.snn_encrypted(P, K, net, ct)
+    for li in range(2):
+        got = O.decrypt(P, K, enc["spikes"][li].reshape(-1, P["n"] + 1)).reshape(3, -1)
+        assert np.array_equal(got, plain["spikes"][li])
+    assert np.array_equal(O.decrypt(P, K, enc["scores"]), plain["scores"])
+
+
+def test_encrypted_conv_snn_static_input(oracle_keys):
+    """Conv layer on pixel ciphertexts computed once and reused each step."""
+    P, K = oracle_keys("T0", 31)
+    g = np.random.default_rng(8)
+    net = {"layers": [{"type": "conv", "W": g.integers(-1, 2, (2, 1, 3, 3)).astype(np.int32),
+                       "cin": 1, "h": 5, "w": 5, "stride": 2, "pad": 0},
+                      {"type": "fc", "W": g.integers(-1, 2, (2, 8)).astype(np.int32)}],
+           "lif": dict(v_th=2, leak_shift=1, spike_scale=1), "T": 2, "static_input": True}
+    img = g.integers(0, 2, 25).astype(np.int32)
+    plain = O.snn_plain(P, net, img)
+    enc = O.snn_encrypted(P, K, net, O.encrypt(P, K, img, 5))
+    got = O.decrypt(P, K, enc["spikes"][0].reshape(-1, P["n"] + 1)).reshape(2, -1)
+    assert np.array_equal(got, plain["spikes"][0])
+    assert np.array_equal(O.decrypt(P, K, enc["scores"]), plain["scores"])
