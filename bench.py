@@ -1,0 +1,337 @@
+"""Benchmark: encrypted MNIST-shaped conv-SNN inference on GB300.
+
+Workload (one "step" = one encrypted prediction of a batch of images, all T
+time steps, every hot-path stage): seeded 28x28 stroke images quantised to
+4 levels, encrypted per pixel (LWE n=630); conv 1->8 5x5 s2 (1152 LIF) ->
+FC 1152->128 LIF -> FC 128->10 LIF with spike-count scores; TFHE n=630, k=1,
+N=1024, Bg=2^7 l=3, key switch 2^2 x 7, p=64 + padding; T=4 (5160
+bootstraps per image, each LIF neuron-step one multi-value bootstrap giving
+FHE-Fire and FHE-Reset).
+
+Prints one JSON line (rank 0).  `value` is PBS/s over the whole job with the
+encrypted inputs resident in HBM; `e2e` is the same metric through the C ABI
+with host buffers (H2D of the encrypted images and D2H of the encrypted
+scores inside the timed region).  `--impl reference` times the CPU oracle on
+the host cores instead (bounded sample per step).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("PBS/s INT8-limb TC vs exact CUDA-core (bit-exact); "
+          "ms per encrypted SNN prediction")
+UNIT = "PBS/s"
+SM_COUNT = 152
+# INT32 multiply-add issue rate of one SM (4 SMSPs x 16 lanes per clock).
+IMAD_PER_SM_CLK = 64
+SM_MAX_MHZ = 2070.0
+# Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
+
+
+def br_macs(P):
+    return P["n"] * (P["k"] + 1) ** 2 * P["l"] * P["N"] ** 2
+
+
+def workload_name(P, T, images):
+    return ("mnist28-csnn conv8x5x5s2-fc128-fc10 LIF, TFHE n=%d N=%d Bg=2^%d l=%d "
+            "ks=2^%dx%d p=%d, T=%d, %d images/step" % (
+                P["n"], P["N"], P["log2_bg"], P["l"], P["log2_bks"], P["l_ks"],
+                1 << P["log2_p"], T, images))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(P, seed, images, n_pbs, nthreads):
+    """Oracle PBS/s on the host cores: n_pbs LIF bootstraps of layer-1
+    neurons (conv WeightSum + centring + multi-value FHE-Fire/FHE-Reset)."""
+    from oracle import oracle as O
+    from paper_2309_09025_gb300 import synth
+    okeys = O.keygen(P, seed)
+    net = synth.csnn_net(T=4)
+    img = images[0].reshape(-1)
+    ct = O.encrypt(P, okeys, img, 1000)
+    conv = net["layers"][0]
+    I = O.lwe_conv2d(P, conv["W"], ct, 1, 28, 28, 2, 0)
+    H = O.lwe_add_const(P, I[:n_pbs], (1 << P["log2_p"]) // 2)
+    luts = O.lif_luts(P, **net["lif"])
+    t0 = time.perf_counter()
+    O.pbs(P, okeys, H, luts, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return n_pbs / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_2309_09025_gb300 import synth
+    P = dict(synth.P630)
+    cores = os.cpu_count() or 1
+    images = synth.stroke_images(5, 1)
+    n_pbs = max(cores, 8)
+    times = []
+    for it in range(args.warmup + args.steps):
+        rate, dt = cpu_oracle_rate(P, 3, images, n_pbs, cores)
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = n_pbs * len(times) / total
+    sample = ("%d layer-1 LIF bootstraps (conv WeightSum + multi-value FHE-Fire/FHE-Reset, "
+              "P630) per step on %d threads" % (n_pbs, cores))
+    per_image = synth_pbs_per_image(T=4)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(P, 4, 1) + " (CPU oracle sample)"},
+        "ms_per_prediction": 1e3 * per_image / value,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def synth_pbs_per_image(T):
+    return (8 * 12 * 12 + 128 + 10) * T
+
+
+def run_ours(args):
+    import torch
+    from paper_2309_09025_gb300 import build, fhe, synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    build.build()
+    P = dict(synth.P630)
+    T = 4
+    B = args.images
+    net = synth.csnn_net(T=T)
+    keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, B * 1152))
+    images = synth.stroke_images(5 + rank, B)
+    ct = fhe.encrypt(keys, images.reshape(-1), seed=11 + rank).view(B, 28 * 28, P["n"] + 1)
+    variant = fhe.VARIANT_TC if args.variant == "tc" else fhe.VARIANT_EXACT
+    if args.variant == "auto":
+        variant = fhe.VARIANT_EXACT
+        try:
+            probe = fhe.Snn(keys, net, max_images=1, variant=fhe.VARIANT_TC, use_graph=False)
+            sc = torch.empty((1, 10, P["n"] + 1), dtype=torch.int32, device="cuda")
+            probe.infer(ct[:1].contiguous(), 1, sc)
+            torch.cuda.synchronize()
+            variant = fhe.VARIANT_TC
+            probe.free()
+        except fhe.FheError:
+            pass
+    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=True, profile=True)
+    per_image = snn.pbs_per_image()
+    scores = torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        snn.infer(ct, B, scores)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    launches0 = fhe.kernel_launches()
+    step_ms, br_ms, br_launches, br_cts = [], 0.0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush (256 MiB > 129 MB L2), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        snn.infer(ct, B, scores)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ms, nl, nc = snn.profile()
+        br_ms += ms
+        br_launches += nl
+        br_cts += nc
+    barrier()
+    launches = fhe.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    total_pbs = per_image * B * args.steps * world
+    value = total_pbs / (total_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.empty(ct.shape, dtype=torch.int32, pin_memory=True)
+        h_in.copy_(ct.cpu())
+        h_out = torch.empty(scores.shape, dtype=torch.int32, pin_memory=True)
+        snn.infer(h_in, B, h_out, on_host=True)  # warm the host path
+        barrier()
+        e2e_ms = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            snn.infer(h_in, B, h_out, on_host=True)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        barrier()
+        e2e_total = sum(e2e_ms)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        e2e = {"value": per_image * B * args.e2e_steps * world / (e2e_total / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_in.numel() * 4),
+               "d2h_bytes_per_step": int(h_out.numel() * 4)}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (blind rotation, measured in the timed region)
+    br_avg_ms = br_ms / max(br_launches, 1)
+    macs_per_launch = br_macs(P) * br_cts / max(br_launches, 1)
+    if variant == fhe.VARIANT_EXACT:
+        achieved = macs_per_launch / (br_avg_ms / 1e3) / 1e12
+        peak = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_blind_rotate_exact<1024,4>",
+                "peak_basis": "152 SMs x 64 INT32 multiply-adds/clk x 2070 MHz (derived)"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        flops = 2.0 * 4 * macs_per_launch  # 4 eight-bit limbs on fp16 tensor cores
+        achieved = flops / (br_avg_ms / 1e3) / 1e12
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "blind rotation (tcgen05)",
+                "peak_basis": "measured bf16 sustained (fp16 same rate), of measured"}
+    roof["launch_ms"] = br_avg_ms
+    roof["launches"] = br_launches
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        n_pbs = max(cores, 8)
+        rate, dt = cpu_oracle_rate(P, 3, images, n_pbs, cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d layer-1 LIF bootstraps at P630 (%.1f s of CPU work)" % (n_pbs, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name(P, T, B), "images_per_step": B,
+                   "variant": "tc" if variant == fhe.VARIANT_TC else "exact",
+                   "cuda_graph_per_time_step": True,
+                   "l2": "256 MiB buffer written before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "ms_per_prediction": total_ms / args.steps / B,
+        "pbs_per_image": per_image,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--images", type=int, default=4)
+    ap.add_argument("--variant", default="auto", choices=["auto", "exact", "tc"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * fhe_dicsnn.h -- C ABI of the GB300 (sm_103a) FHE-DiCSNN hot path.
+ *
+ * The library evaluates the paper's encrypted spiking network (FHE-DiCSNN):
+ * TFHE programmable bootstrapping of LWE ciphertexts over the uint32 torus
+ * (paper 2.1, Thm 2.1), the integer-weighted LWE sums that feed it (4.1,
+ * Eq. "noise grows"), and the LIF neuron's Fire/Reset as bootstrap test
+ * polynomials (4.2, Eqs. FHE-Fire / FHE-Reset; discretized LIF of Thm 3.2).
+ *
+ * Conventions shared by every entry point
+ *  - Torus: q = 2^32; ciphertext words are uint32_t and wrap modulo 2^32.
+ *  - LWE ciphertext: n+1 consecutive uint32_t, mask a[0..n-1] then body b.
+ *    Arrays of ciphertexts are dense [count][n+1] (no padding).
+ *  - Messages: p = 2^log2_p with one padding bit, Delta = 2^(31 - log2_p);
+ *    a message m is encoded as m * Delta (mod 2^32), so messages live in
+ *    Z_{2p} and decrypt to the signed range [-p, p).
+ *  - Pointers documented "device" must be CUDA device memory of the current
+ *    device (for instance torch tensors' data_ptr()); "host" pointers are
+ *    ordinary host memory.  The caller owns every buffer it passes; the
+ *    library owns the opaque handles it returns.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work is enqueued asynchronously on it; the functions return
+ *    once the work is enqueued, except where stated.
+ *  - Errors: functions return 0 (FHE_OK) or a negative FHE_E* code; they
+ *    never throw.  An asynchronous kernel failure is reported by the next
+ *    call that synchronizes (fhe_status, fhe_keys_export, fhe_snn_infer).
+ *  - Handles are not thread-safe: a fhe_keys (and its workspace) must not be
+ *    used by two calls that overlap in time.
+ */
+#ifndef FHE_DICSNN_H
+#define FHE_DICSNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHE_OK 0
+#define FHE_EINVAL (-1)        /* bad argument, size or parameter set          */
+#define FHE_ENOMEM (-2)        /* device or host allocation failed             */
+#define FHE_ECUDA (-3)         /* a CUDA runtime call or kernel failed         */
+#define FHE_ETIMEOUT (-4)      /* a bounded device wait gave up (status word)  */
+#define FHE_EUNSUPPORTED (-5)  /* valid but not implemented on this path       */
+
+/* Blind-rotation variants accepted by fhe_pbs_batch / fhe_snn_create. */
+#define FHE_VARIANT_EXACT 0 /* exact uint32 external product on CUDA cores (IMAD) */
+#define FHE_VARIANT_TC 1    /* exact external product on tcgen05 tensor cores,
+                               key split into 8-bit limbs (fp16 operands, fp32
+                               accumulation kept below 2^24)                 */
+
+/* Which key to export (fhe_keys_export / fhe_keys_size). */
+#define FHE_KEY_LWE 0  /* s:   uint32_t[n], entries 0/1                        */
+#define FHE_KEY_GLWE 1 /* S:   uint32_t[k*N], entries 0/1                      */
+#define FHE_KEY_BSK 2  /* ek:  uint32_t[n][(k+1)*l][k+1][N]: row (j, lam) at
+                          index j*l + lam-1 is a GLWE encryption of zero with
+                          s_i * 2^(32 - lam*log2_bg) added to component j  */
+#define FHE_KEY_KSK 3  /* ksk: uint32_t[k*N][l_ks][n+1]: LWE_s(z_i * 2^(32 -
+                          lam*log2_bks)) for lam = 1..l_ks                   */
+
+/* TFHE parameter set.  Noise standard deviations are powers of two given by
+ * their negative log2 in torus units (sigma = 2^-x); x >= 64 means no noise.
+ * Supported: k = 1; N in {256, 512, 1024, 2048}; log2_bg * l <= 32,
+ * log2_bg <= 15, l <= 4; log2_bks * l_ks <= 32, log2_bks <= 7; 1 <= log2_p
+ * <= 10 with 2p <= N; 1 <= n <= 2048.                                     */
+typedef struct fhe_params {
+  uint32_t n;        /* LWE dimension                                        */
+  uint32_t k;        /* GLWE dimension (must be 1)                           */
+  uint32_t N;        /* polynomial size                                      */
+  uint32_t log2_bg;  /* gadget base Bg = 2^log2_bg                           */
+  uint32_t l;        /* gadget levels                                        */
+  uint32_t log2_bks; /* key-switching base                                   */
+  uint32_t l_ks;     /* key-switching levels                                 */
+  uint32_t log2_p;   /* message modulus p = 2^log2_p                         */
+  int32_t lwe_noise_log2;
+  int32_t glwe_noise_log2;
+} fhe_params;
+
+typedef struct fhe_keys fhe_keys; /* opaque: device keys + PBS workspace   */
+typedef struct fhe_lut fhe_lut;   /* opaque: device test polynomial(s)     */
+typedef struct fhe_snn fhe_snn;   /* opaque: encrypted network + state     */
+
+/* Human-readable text of an FHE_E* code (static storage). */
+const char *fhe_strerror(int code);
+
+/* Key generation from a seed (paper 2.1: LWE/RLWE keys, bootstrapping key
+ * ek = (RGSW(X^s_1), ..., RGSW(X^s_n)), key-switching key).  All draws are
+ * SplitMix64 outputs addressed by (seed, domain, index), so the keys are a
+ * pure function of (params, seed).  Runs on the current CUDA device, on
+ * `stream`, and allocates the device keys plus a PBS workspace for
+ * `max_batch` ciphertexts (0 = 16384).  *out receives the handle.
+ * Errors: FHE_EINVAL (NULL pointer, unsupported parameter set),
+ * FHE_ENOMEM, FHE_ECUDA. */
+int fhe_keygen_from_seed(const fhe_params *params, uint64_t seed, size_t max_batch,
+                         void *stream, fhe_keys **out);
+
+/* Free a key handle (synchronizes the device first).  NULL is ignored. */
+void fhe_keys_free(fhe_keys *keys);
+
+/* Parameter set the keys were generated for. */
+int fhe_keys_params(const fhe_keys *keys, fhe_params *out);
+
+/* Size in bytes of key `which` (FHE_KEY_*); 0 on a bad argument. */
+size_t fhe_keys_size(const fhe_keys *keys, int which);
+
+/* Copy key `which` in the layout documented at FHE_KEY_* to host memory
+ * `host_dst` of `bytes` bytes (must equal fhe_keys_size).  Synchronizes.
+ * Errors: FHE_EINVAL, FHE_ECUDA. */
+int fhe_keys_export(const fhe_keys *keys, int which, void *host_dst, size_t bytes);
+
+/* LWE encryption (paper 2.1, LWE): ct[i] = (a, <a,s> + e + msg[i]*Delta).
+ * msg: device int32[count], any integer (reduced mod 2p).  ct: device
+ * uint32[count][n+1].  Masks and noise are draws of (seed, index i), so the
+ * same seed re-encrypts identically.  Errors: FHE_EINVAL, FHE_ECUDA. */
+int fhe_encrypt(const fhe_keys *keys, const int32_t *msg, size_t count, uint64_t seed,
+                uint32_t *ct, void *stream);
+
+/* LWE decryption: msg[i] = round((b - <a,s>) / Delta) as a signed value in
+ * [-p, p).  ct: device uint32[count][n+1]; msg: device int32[count]. */
+int fhe_decrypt(const fhe_keys *keys, const uint32_t *ct, size_t count, int32_t *msg,
+                void *stream);
+
+/* Homomorphic WeightSum for a fully connected layer (paper 4.1, Eq. "noise
+ * grows"): for every batch item b and output i,
+ *   ct_out[b][i] = sum_j W[i][j] * ct_in[b][j]  (+ bias[i] * Delta on b),
+ * componentwise modulo 2^32.  W: device int32[M][K] row-major; bias: device
+ * int32[M] or NULL; ct_in: device uint32[batch][K][n+1]; ct_out: device
+ * uint32[batch][M][n+1] (must not alias ct_in). */
+int fhe_lwe_linear(uint32_t n, uint32_t log2_p, const int32_t *W, size_t M, size_t K,
+                   const int32_t *bias, const uint32_t *ct_in, size_t batch, uint32_t *ct_out,
+                   void *stream);
+
+/* Convolution as WeightSum over receptive fields (paper 4.1; conv layer of
+ * 3.1).  ct_in: device uint32[batch][cin][h][w][n+1]; W: device
+ * int32[cout][cin][kh][kw]; bias: device int32[cout] or NULL; zero padding
+ * reads trivial encryptions of 0; ct_out: device
+ * uint32[batch][cout][ho][wo][n+1] with ho = (h + 2 pad - kh)/stride + 1. */
+int fhe_lwe_conv2d(uint32_t n, uint32_t log2_p, const int32_t *W, uint32_t cin, uint32_t h,
+                   uint32_t w, uint32_t cout, uint32_t kh, uint32_t kw, uint32_t stride,
+                   uint32_t pad, const int32_t *bias, const uint32_t *ct_in, size_t batch,
+                   uint32_t *ct_out, void *stream);
+
+/* Bootstrap look-up tables.  f: host int32[L][p], f[j][u] is the value
+ * (any integer, reduced mod 2p) the bootstrap returns for message u in
+ * [0, p); messages u in [p, 2p) return -f[j][u - p] (negacyclic half of
+ * Thm 2.1).  L = 1: the test polynomial is Delta * f on centred boxes
+ * round(i p / N).  L = 2: one blind rotation serves both tables (the
+ * FHE-Fire / FHE-Reset pair of 4.2) through the multi-value split
+ * ACC_j = (1 - X) coeffs(f_j) * ACC of the constant test polynomial
+ * (Delta/2) sum X^i.  The handle uploads the tables once (synchronous). */
+int fhe_lut_create(const fhe_keys *keys, const int32_t *f, uint32_t L, fhe_lut **out);
+void fhe_lut_free(fhe_lut *lut);
+
+/* Programmable bootstrapping of a batch (paper Thm 2.1, bootstrapping =
+ * KeySwitch o Extract o BlindRotate o Initialize): for every input i and
+ * table j, ct_out[j][i] = LWE_s(f_j(m_i)).  ct_in: device uint32[count][n+1];
+ * ct_out: device uint32[L][count][n+1] (must not alias ct_in).  variant:
+ * FHE_VARIANT_EXACT or FHE_VARIANT_TC (both bit-identical).  Uses the key
+ * handle's workspace; batches above its capacity run in chunks.
+ * Errors: FHE_EINVAL, FHE_EUNSUPPORTED (variant not built for these
+ * parameters), FHE_ECUDA. */
+int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+                  uint32_t *ct_out, int variant, void *stream);
+
+/* Device status word: FHE_OK, or FHE_ETIMEOUT if a bounded device wait gave
+ * up since the last call.  Synchronizes `stream`, then clears the word. */
+int fhe_status(fhe_keys *keys, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Encrypted DiCSNN inference (paper 3.1-3.3 network, 4.1-4.2 evaluation,
+ * 5.3 client/server flow).  A network is a chain of layers, each a WeightSum
+ * (conv or fully connected) followed by a LIF spiking activation layer:
+ *   I = WeightSum(x);  H = V + I;
+ *   (S, V) = bootstrap(H + p/2) with the FHE-Fire / FHE-Reset tables;
+ *   x_next = S;  scores += S of the last layer.
+ * The first layer's input is either static (pixel ciphertexts reused every
+ * step, the conv output computed once) or a per-step spike train.
+ */
+#define FHE_LAYER_FC 0
+#define FHE_LAYER_CONV 1
+
+typedef struct fhe_layer_desc {
+  int32_t type;            /* FHE_LAYER_FC or FHE_LAYER_CONV                  */
+  const int32_t *weights;  /* HOST int32: FC [out][in]; conv [cout][cin][kh][kw] */
+  uint32_t in_size;        /* FC: number of inputs                           */
+  uint32_t out_size;       /* FC: number of outputs                          */
+  uint32_t cin, h, w, cout, kh, kw, stride, pad; /* conv geometry          */
+} fhe_layer_desc;
+
+typedef struct fhe_snn_desc {
+  uint32_t n_layers;
+  const fhe_layer_desc *layers; /* host array of n_layers descriptors        */
+  int32_t v_th;                 /* LIF threshold V_th (Thm 3.2)               */
+  int32_t leak_shift;           /* leak(v) = v >> leak_shift; 0 = IF model    */
+  int32_t spike_scale;          /* value of an output spike (1 or 2)         */
+  uint32_t T;                   /* time steps                                */
+  int32_t static_input;         /* 1: input reused every step (pixels)       */
+  uint32_t max_images;          /* capacity: images per inference call       */
+  int32_t variant;              /* FHE_VARIANT_* of the bootstraps           */
+  int32_t use_graph;            /* bit 0: capture each time step as a CUDA
+                                   graph; bit 1 (FHE_SNN_PROFILE): time the
+                                   blind rotations (fhe_snn_profile)        */
+} fhe_snn_desc;
+
+/* Build a network on `keys` (uploads weights, allocates state for
+ * max_images images; synchronous).  Errors: FHE_EINVAL, FHE_ENOMEM. */
+int fhe_snn_create(fhe_keys *keys, const fhe_snn_desc *desc, fhe_snn **out);
+void fhe_snn_free(fhe_snn *net);
+
+/* Number of bootstraps (blind rotations) one inference of one image runs. */
+uint64_t fhe_snn_pbs_per_image(const fhe_snn *net);
+
+/* Encrypted inference of `n_images` images (<= max_images).
+ * ct_input: uint32 [n_images][n_in][n+1] if static_input, else
+ *           [T][n_images][n_in][n+1] (time-major);
+ * scores:   uint32 [n_images][n_out][n+1] (encrypted spike counts).
+ * If inputs_on_host != 0 both pointers are HOST memory: the call copies the
+ * inputs to the device, runs the network and copies the scores back, then
+ * synchronizes `stream` (end-to-end client/server round trip, 5.3).
+ * Otherwise both are device pointers and the call only enqueues work.
+ * Errors: FHE_EINVAL, FHE_ECUDA, FHE_ETIMEOUT. */
+int fhe_snn_infer(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
+                  int inputs_on_host, void *stream);
+
+/* Optional: device spike ciphertexts of layer `layer` at the last step of
+ * the last inference, copied to device buffer dst [n_images][size][n+1]. */
+int fhe_snn_layer_spikes(const fhe_snn *net, uint32_t layer, uint32_t *dst, void *stream);
+
+/* Blind-rotation kernel time of the last inference (instrumentation).  When
+ * the network was created with profiling on (FHE_SNN_PROFILE in use_graph's
+ * bit 1), every blind-rotation launch is bracketed by a CUDA event pair on its
+ * stream, inside the captured graphs too.  Synchronizes, then writes the
+ * summed milliseconds, the number of launches and the number of bootstrapped
+ * ciphertexts of the last fhe_snn_infer call.  Errors: FHE_EINVAL when
+ * profiling is off, FHE_ECUDA. */
+#define FHE_SNN_PROFILE 2
+int fhe_snn_profile(const fhe_snn *net, double *br_ms, uint64_t *br_launches,
+                    uint64_t *br_ciphertexts);
+
+/* Process-wide count of kernels this library has launched (graph replays
+ * count every kernel node of the graph). */
+uint64_t fhe_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHE_DICSNN_H */

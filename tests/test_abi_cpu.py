@@ -1,0 +1,41 @@
+"""CPU checks of the C ABI library: it builds, loads without a GPU and
+exports every entry point the header declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "fhe_dicsnn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fhe_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2309_09025_gb300 import build, fhe
+    path = build.build()
+    L = ctypes.CDLL(path)
+    declared = _declared()
+    assert len(declared) >= 15
+    missing = [s for s in declared if not hasattr(L, s)]
+    assert not missing, missing
+    assert sorted(fhe.EXPORTED) == declared
+
+
+def test_strerror_without_gpu():
+    from paper_2309_09025_gb300 import fhe
+    assert fhe.strerror(0) == "ok"
+    assert "invalid" in fhe.strerror(fhe.FHE_EINVAL)
+    assert fhe.strerror(12345) == "unknown error"
+
+
+def test_unsupported_params_rejected_before_any_device_work():
+    from paper_2309_09025_gb300 import fhe, synth
+    p = fhe.Params.from_dict(dict(synth.P64, k=2))
+    h = ctypes.c_void_p()
+    rc = fhe.lib().fhe_keygen_from_seed(ctypes.byref(p), 1, 0, None, ctypes.byref(h))
+    assert rc == fhe.FHE_EINVAL and not h.value
+    rc = fhe.lib().fhe_keygen_from_seed(None, 1, 0, None, ctypes.byref(h))
+    assert rc == fhe.FHE_EINVAL

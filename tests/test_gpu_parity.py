@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Exact paths must be bit-identical to the oracle for the same seeds (keys,
+encryptions, WeightSums, bootstraps).  Sizes span several CTAs and a ragged
+tail; the full-size P630/P750 cases compare sampled outputs that the oracle
+computes one by one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2309_09025_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_09025_gb300 import build, fhe as F
+    build.build()
+    return F
+
+
+_GPU_KEYS = {}
+
+
+def gpu_keys(fhe, name, seed, max_batch=0, **over):
+    key = (name, seed, max_batch, tuple(sorted(over.items())))
+    if key not in _GPU_KEYS:
+        P = dict(synth.PRESETS[name])
+        P.update(over)
+        _GPU_KEYS[key] = (P, fhe.keygen_from_seed(P, seed, max_batch=max_batch))
+    return _GPU_KEYS[key]
+
+
+def u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("name,seed", [("P64", 1), ("T0", 2), ("P630", 3)])
+def test_keygen_bit_exact(fhe, oracle_keys, name, seed):
+    P, K = gpu_keys(fhe, name, seed)
+    _, OK = oracle_keys(name, seed)
+    assert np.array_equal(K.export(fhe.KEY_LWE), OK["lwe_key"])
+    assert np.array_equal(K.export(fhe.KEY_GLWE), OK["glwe_key"])
+    assert np.array_equal(K.export(fhe.KEY_BSK), OK["bsk"])
+    assert np.array_equal(K.export(fhe.KEY_KSK), OK["ksk"])
+
+
+@pytest.mark.parametrize("name", ["P64", "P630"])
+def test_encrypt_decrypt_bit_exact(fhe, oracle_keys, name):
+    P, K = gpu_keys(fhe, name, 5)
+    _, OK = oracle_keys(name, 5)
+    p = 1 << P["log2_p"]
+    m = np.concatenate([np.arange(-p, p), synth.uniform_messages(9, 997, p)]).astype(np.int32)
+    ct = fhe.encrypt(K, m, seed=44)
+    assert np.array_equal(u32(ct), O.encrypt(P, OK, m, 44))
+    assert np.array_equal(fhe.decrypt(K, ct).cpu().numpy(), ((m + p) % (2 * p)) - p)
+    # empty batches are no-ops
+    fhe.encrypt(K, np.zeros(0, np.int32), seed=1)
+
+
+def test_lwe_linear_bit_exact(fhe, oracle_keys):
+    P = dict(synth.P630)
+    g = np.random.default_rng(3)
+    K_in, M, batch = 67, 45, 3  # ragged against the 32 x 128 tiles
+    W = g.integers(-15, 16, (M, K_in)).astype(np.int32)
+    bias = g.integers(-5, 6, M).astype(np.int32)
+    ct = g.integers(0, 2 ** 32, (batch, K_in, P["n"] + 1), dtype=np.uint64).astype(np.uint32)
+    out = fhe.lwe_linear(P, torch.from_numpy(W).cuda(), ct, bias=torch.from_numpy(bias).cuda())
+    for b in range(batch):
+        assert np.array_equal(u32(out[b]), O.lwe_linear(P, W, ct[b], bias))
+
+
+def test_lwe_conv2d_bit_exact(fhe):
+    P = dict(synth.P630)
+    g = np.random.default_rng(4)
+    W = g.integers(-15, 16, (8, 1, 5, 5)).astype(np.int32)
+    ct = g.integers(0, 2 ** 32, (2, 28 * 28, P["n"] + 1), dtype=np.uint64).astype(np.uint32)
+    out = fhe.lwe_conv2d(P, torch.from_numpy(W).cuda(), ct, 1, 28, 28, 2, 0, batch=2)
+    for b in range(2):
+        assert np.array_equal(u32(out[b]), O.lwe_conv2d(P, W, ct[b], 1, 28, 28, 2, 0))
+    W2 = g.integers(-3, 4, (3, 2, 3, 3)).astype(np.int32)
+    ct2 = g.integers(0, 2 ** 32, (1, 2 * 7 * 6, P["n"] + 1), dtype=np.uint64).astype(np.uint32)
+    out2 = fhe.lwe_conv2d(P, torch.from_numpy(W2).cuda(), ct2, 2, 7, 6, 2, 1)
+    assert np.array_equal(u32(out2[0]), O.lwe_conv2d(P, W2, ct2[0], 2, 7, 6, 2, 1))
+
+
+def _luts(P, L):
+    p = 1 << P["log2_p"]
+    if L == 1:
+        return synth.identity_plus_threshold_lut(p)[None]
+    return O.lif_luts(P, v_th=8 if p >= 32 else 2, leak_shift=1, spike_scale=1)
+
+
+VARIANTS = ["EXACT"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", [1, 2])
+def test_pbs_p64_bit_exact_all_messages(fhe, oracle_keys, variant, L):
+    P, K = gpu_keys(fhe, "P64", 1)
+    _, OK = oracle_keys("P64", 1)
+    p = 1 << P["log2_p"]
+    m = np.concatenate([np.arange(2 * p), synth.uniform_messages(2, 37, 2 * p)]).astype(np.int32)
+    ct = O.encrypt(P, OK, m, 123)  # 101 ciphertexts: ragged against 8 per CTA
+    luts = _luts(P, L)
+    lut = fhe.lut_create(K, luts)
+    out = fhe.pbs_batch(K, ct, lut, getattr(fhe, "VARIANT_" + variant))
+    torch.cuda.synchronize()
+    ref = O.pbs(P, OK, ct, luts, nthreads=NTHREADS)
+    assert np.array_equal(u32(out), ref)
+    assert K.status() == fhe.FHE_OK
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pbs_t0_brute_force_and_bit_exact(fhe, oracle_keys, variant):
+    P, K = gpu_keys(fhe, "T0", 2)
+    _, OK = oracle_keys("T0", 2)
+    p = 1 << P["log2_p"]
+    m = np.arange(2 * p, dtype=np.int32)
+    ct = O.encrypt(P, OK, m, 5)
+    for L in (1, 2):
+        luts = _luts(P, L)
+        out = fhe.pbs_batch(K, ct, fhe.lut_create(K, luts), getattr(fhe, "VARIANT_" + variant))
+        got = u32(out)
+        for j in range(L):
+            dec = O.decrypt(P, OK, got[j])
+            fe = np.concatenate([luts[j], -luts[j]]).astype(np.int64)
+            assert np.array_equal(dec, ((fe + p) % (2 * p)) - p)
+        ref = O.pbs(P, OK, ct, luts, nthreads=NTHREADS)
+        assert np.array_equal(got, ref)
+
+
+def test_pbs_chunked_workspace_and_edges(fhe, oracle_keys):
+    """Batches above the workspace capacity run in chunks; 0 and 1 items."""
+    P, K = gpu_keys(fhe, "P64", 1, max_batch=24)
+    _, OK = oracle_keys("P64", 1)
+    p = 1 << P["log2_p"]
+    m = synth.uniform_messages(17, 61, p)
+    ct = O.encrypt(P, OK, m, 8)
+    luts = _luts(P, 2)
+    lut = fhe.lut_create(K, luts)
+    out = fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT)
+    assert np.array_equal(u32(out), O.pbs(P, OK, ct, luts, nthreads=NTHREADS))
+    one = fhe.pbs_batch(K, ct[:1], lut, fhe.VARIANT_EXACT)
+    assert np.array_equal(u32(one), O.pbs(P, OK, ct[:1], luts))
+    empty = torch.empty((2, 0, P["n"] + 1), dtype=torch.int32, device="cuda")
+    fhe.pbs_batch(K, torch.empty((0, P["n"] + 1), dtype=torch.int32, device="cuda"), lut,
+                  fhe.VARIANT_EXACT, out=empty)
+
+
+@pytest.mark.parametrize("name,count", [("P630", 1523), ("P750", 613)])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pbs_full_size_sampled(fhe, oracle_keys, name, count, variant):
+    """Full-size parameter sets: a batch spanning many CTAs with a ragged
+    tail; sampled outputs bit-exact to the oracle, every output decrypting to
+    the table value or a neighbouring box (modulus-switch failures)."""
+    P, K = gpu_keys(fhe, name, 3)
+    _, OK = oracle_keys(name, 3)
+    p = 1 << P["log2_p"]
+    m = synth.uniform_messages(31, count, p)
+    ct = fhe.encrypt(K, m, seed=99)
+    luts = _luts(P, 1)
+    out = fhe.pbs_batch(K, ct, fhe.lut_create(K, luts), getattr(fhe, "VARIANT_" + variant))
+    got = u32(out)[0]
+    octs = O.encrypt(P, OK, m, 99)
+    assert np.array_equal(u32(ct), octs)
+    idx = np.array([0, 1, 2, 3, count // 2, count - 3, count - 2, count - 1])
+    ref = O.pbs(P, OK, octs[idx], luts, nthreads=NTHREADS)[0]
+    assert np.array_equal(got[idx], ref)
+    dec = O.decrypt(P, OK, got).astype(np.int64)
+    exp = luts[0][m].astype(np.int64)
+    diff = (dec - exp + p) % (2 * p) - p
+    assert np.abs(diff).max() <= 2
+    assert np.mean(diff != 0) < 0.25
+
+
+def test_snn_toy_layer_bit_exact(fhe, oracle_keys):
+    """16 Bernoulli(0.3) spikes -> 32 LIF neurons, T = 2 (64 bootstraps)."""
+    P, K = gpu_keys(fhe, "P64", 1)
+    _, OK = oracle_keys("P64", 1)
+    net = synth.toy_lif_net(seed=1)
+    x = synth.bernoulli_spikes(1, 2, 16, 0.3)
+    ct = O.encrypt(P, OK, x.reshape(-1), 7).reshape(1, 2, 16, -1)
+    for use_graph in (False, True):
+        snn = fhe.Snn(K, net, max_images=1, use_graph=use_graph)
+        assert snn.pbs_per_image() == 64
+        scores = torch.empty((1, 32, P["n"] + 1), dtype=torch.int32, device="cuda")
+        snn.infer(torch.from_numpy(ct.view(np.int32)).cuda(), 1, scores)
+        ref = O.snn_encrypted(P, OK, net, ct[0], nthreads=NTHREADS)
+        assert np.array_equal(u32(scores)[0], ref["scores"])
+
+
+def test_snn_csnn_topology_small_params_bit_exact(fhe, oracle_keys):
+    """The MNIST-shaped conv-SNN (conv 5x5 s2 -> 1152 LIF -> FC 128 LIF ->
+    FC 10 LIF) end to end on 2 images with the small ring (N=256, p=64),
+    scores bit-exact to the oracle; host buffers through the C ABI."""
+    P, K = gpu_keys(fhe, "P64", 9, log2_p=6)
+    _, OK = oracle_keys("P64", 9, log2_p=6)
+    net = synth.csnn_net(seed=2, T=2)
+    imgs = synth.stroke_images(3, 2).reshape(2, -1)
+    ct = np.stack([O.encrypt(P, OK, imgs[i], 100 + i) for i in range(2)])
+    snn = fhe.Snn(K, net, max_images=2, use_graph=True)
+    scores = np.zeros((2, 10, P["n"] + 1), np.uint32)
+    snn.infer(np.ascontiguousarray(ct), 2, scores, on_host=True)
+    for i in range(2):
+        ref = O.snn_encrypted(P, OK, net, ct[i], nthreads=NTHREADS)
+        assert np.array_equal(scores[i], ref["scores"])
