@@ -132,10 +132,15 @@ struct fhe_lut {
   uint32_t off[2];
 };
 
+// On failure, also clear the runtime's last-error slot so that a
+// recoverable error does not resurface in later, unrelated checks.
 #define FHE_CUDA_TRY(expr)                        \
   do {                                            \
     cudaError_t _e = (expr);                      \
-    if (_e != cudaSuccess) return FHE_ECUDA;      \
+    if (_e != cudaSuccess) {                      \
+      (void)cudaGetLastError();                   \
+      return FHE_ECUDA;                           \
+    }                                             \
   } while (0)
 
 namespace fhe {

@@ -41,6 +41,11 @@ struct fhe_snn {
   size_t graph_images;
   std::vector<cudaGraphExec_t> graphs;  // one per time step
   std::vector<int64_t> graph_kernels;   // kernel nodes of each graph
+  // Graphs are captured and replayed on a library-owned non-blocking stream
+  // (the legacy default stream cannot be captured), joined to the caller's
+  // stream by the two events below.
+  cudaStream_t gs;
+  cudaEvent_t join_in, join_out;
   size_t last_images;
   // instrumentation: one event pair per (step, layer) blind rotation
   bool profile;
@@ -54,6 +59,9 @@ static void snn_release(fhe_snn *S) {
     if (g) cudaGraphExecDestroy(g);
   for (auto &e : S->ev)
     if (e) cudaEventDestroy(e);
+  if (S->join_in) cudaEventDestroy(S->join_in);
+  if (S->join_out) cudaEventDestroy(S->join_out);
+  if (S->gs) cudaStreamDestroy(S->gs);
   for (auto &L : S->layers) {
     cudaFree(L.d_w); cudaFree(L.d_I); cudaFree(L.d_H); cudaFree(L.d_out);
   }
@@ -129,6 +137,11 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   if (cudaMalloc(&S->d_input, sizeof(uint32_t) * in_words) != cudaSuccess ||
       cudaMalloc(&S->d_scores, sizeof(uint32_t) * (size_t)d->max_images * S->n_out * W) != cudaSuccess) {
     snn_release(S); return FHE_ENOMEM;
+  }
+  if (cudaStreamCreateWithFlags(&S->gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->join_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->join_out, cudaEventDisableTiming) != cudaSuccess) {
+    snn_release(S); return FHE_ECUDA;
   }
   S->profile = (d->use_graph & FHE_SNN_PROFILE) != 0;
   if (S->profile) {
@@ -249,14 +262,18 @@ extern "C" int fhe_snn_infer(fhe_snn *S, const uint32_t *ct_input, size_t ni, ui
   FHE_CUDA_TRY(cudaMemcpyAsync(S->d_input, ct_input, sizeof(uint32_t) * in_words,
                                inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
   if (S->desc.use_graph & 1) {
+    FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
+    FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
     if (S->graph_images != ni || S->graphs.size() != S->desc.T) {
-      int rc = snn_capture(S, ni, st);
+      int rc = snn_capture(S, ni, S->gs);
       if (rc) return rc;
     }
     for (uint32_t t = 0; t < S->desc.T; ++t) {
-      FHE_CUDA_TRY(cudaGraphLaunch(S->graphs[t], st));
+      FHE_CUDA_TRY(cudaGraphLaunch(S->graphs[t], S->gs));
       fhe::note_launches(S->graph_kernels[t]);
     }
+    FHE_CUDA_TRY(cudaEventRecord(S->join_out, S->gs));
+    FHE_CUDA_TRY(cudaStreamWaitEvent(st, S->join_out, 0));
   } else {
     for (uint32_t t = 0; t < S->desc.T; ++t) {
       int rc = snn_step(S, t, ni, st);

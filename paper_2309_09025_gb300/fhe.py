@@ -97,7 +97,7 @@ def lib():
             "fhe_encrypt": (ctypes.c_int, [vp, vp, sz, u64, vp, vp]),
             "fhe_decrypt": (ctypes.c_int, [vp, vp, sz, vp, vp]),
             "fhe_lwe_linear": (ctypes.c_int, [u32, u32, vp, sz, sz, vp, vp, sz, vp, vp]),
-            "fhe_lwe_conv2d": (ctypes.c_int, [u32, u32, vp] + [u32] * 9 + [vp, vp, sz, vp, vp]),
+            "fhe_lwe_conv2d": (ctypes.c_int, [u32, u32, vp] + [u32] * 8 + [vp, vp, sz, vp, vp]),
             "fhe_lut_create": (ctypes.c_int, [vp, vp, u32, ctypes.POINTER(vp)]),
             "fhe_lut_free": (None, [vp]),
             "fhe_pbs_batch": (ctypes.c_int, [vp, vp, sz, vp, vp, ctypes.c_int, vp]),
