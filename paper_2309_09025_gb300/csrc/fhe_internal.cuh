@@ -152,6 +152,9 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
               uint32_t *ct_out, cudaStream_t st);
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
            uint32_t *ct_out, cudaStream_t st);
+// Builds the variant's key layout and workspace ahead of the first call
+// (FHE_OK for variants without one; FHE_EUNSUPPORTED for unsupported sets).
+int pbs_prepare(fhe_keys *K, int variant);
 int key_switch_batch(const fhe_keys *K, const uint32_t *d_big, size_t count, uint32_t *ct_out,
                      cudaStream_t st);
 }  // namespace fhe

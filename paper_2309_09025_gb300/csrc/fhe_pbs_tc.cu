@@ -1,12 +1,587 @@
-// fhe_pbs_tc.cu -- tensor-core (tcgen05) variant of the blind rotation.
+// fhe_pbs_tc.cu -- blind rotation with the external product on tcgen05 tensor
+// cores, bit-exact to the uint32 definition (paper 2.1, Blind Rotation;
+// Thm 2.1).
+//
+// The external product of one CMux step is, per output polynomial j,
+//   out_j[c] = sum_r sum_t D_r[t] * ext_{r,j}(c - t),   ext(x) = K[x] (x >= 0),
+//                                                        -K[x+N] (x < 0),
+// a negacyclic (block-Toeplitz) contraction of small signed gadget digits D
+// against 32-bit key words K.  Reversing the digit index (t' = N-1-t) turns
+// the key matrix into a Hankel matrix H[c][t'] = h[c + t'].
+//
+// Exactness.  Key words are split into four balanced 8-bit limbs
+// (K = sum_L 2^(8L) K_L mod 2^32, K_L in [-128, 128)); digits lie in
+// [-Bg/2, Bg/2).  Both are exact fp16 integers, so a tcgen05 kind::f16 MMA
+// with fp32 accumulation is exact as long as every partial sum stays within
+// 2^24: the accumulator is drained (cvt to int32, shifted by 8L, added modulo
+// 2^32) after at most 2^24 / (Bg/2 * 128) terms.
+//
+// Operands (SWIZZLE_NONE, K-major, 8x8 fp16 core matrices of 128 bytes):
+//  - A = digits, M = 128 ciphertexts, tiles of 128 x 64 (LBO 128, SBO 1024);
+//    written once per step to global memory and multicast by cp.async.bulk to
+//    the four CTAs of the cluster (each CTA issues one quarter);
+//  - B = Hankel key, N = 256 output coefficients.  Core matrix delta holds
+//    h[8 delta + rho + kappa]; with LBO = SBO = 128 bytes the matrix
+//    descriptor walks one strip of core matrices for both the N and K
+//    directions, so one 20 KB window per (key row r, limb) feeds all 64 K16
+//    steps of a 256-coefficient block.
+//  - D = TMEM fp32, 128 lanes (ciphertexts) x 256 columns, double buffered.
+//
+// Cluster of 4 CTAs (one per SM) = 128 ciphertexts.  CTA q owns output
+// polynomial j = q / 2, coefficients [512 (q % 2), +512) in two blocks of
+// 256, all limbs.  Per step: digits (all warps) -> cluster barrier -> units
+// (block, limb, chunk) run by a producer warp (bulk copies), an MMA warp and
+// eight epilogue warps (TMEM -> registers, limb recombination, ACC update in
+// global memory) -> cluster barrier.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "fhe_internal.cuh"
 
+using fhe::Params;
+
+namespace {
+
+constexpr int kCluster = 4;
+constexpr int kBt = 128;          // ciphertexts per cluster (MMA M)
+constexpr int kBN = 256;          // output coefficients per block (MMA N)
+constexpr int kKB = 64;           // K elements per A tile
+constexpr int kAStages = 6;
+constexpr int kATile = kBt * kKB * 2;   // 16 KB
+constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
+constexpr int kTmemCols = 512;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait (two seconds).  Sets *abort and returns false when it gives up;
+// returns false immediately once aborted.
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (*abort) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (global_ns() - t0 > 2000000000ull) { *abort = 1; return false; }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, uint32_t bytes,
+                                                   uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_commit_multicast(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: SWIZZLE_NONE, K-major, version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor: kind::f16, A = B = fp16, D = fp32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Balanced 8-bit limb L of a 32-bit word: w = sum_L 2^(8L) limb_L mod 2^32.
+__device__ __forceinline__ int32_t limb8(uint32_t w, uint32_t L) {
+  int32_t v = 0;
+  for (uint32_t i = 0; i <= L; ++i) {
+    v = (int32_t)((w & 0xFFu) ^ 0x80u) - 0x80;
+    w = (w - (uint32_t)v) >> 8;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- key layout
+// strips[((i * R + r) * 2 + j) * 4 + L][delta][rho][kappa] = limb_L(h[8 delta
+// + rho + kappa]), h[s] = ext_{r,j}(s - (N - 1)); 256 core matrices of
+// 8x8 fp16 per strip (the last one is padding).
+__global__ void k_hankel_strips(Params P, const uint32_t *__restrict__ bsk, __half *strips) {
+  const uint32_t N = P.N, R = P.rows();
+  const uint32_t ncm = N / 4u;  // core matrices per strip
+  const uint64_t rows_total = (uint64_t)P.n * R * 2u * 4u * ncm * 8u;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows_total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t rho = (uint32_t)(e % 8u);
+    const uint32_t delta = (uint32_t)((e / 8u) % ncm);
+    const uint64_t strip = e / (8u * ncm);  // ((i R + r) 2 + j) 4 + L
+    const uint32_t L = (uint32_t)(strip % 4u);
+    const uint32_t j = (uint32_t)((strip / 4u) % 2u);
+    const uint64_t ir = strip / 8u;  // i * R + r
+    const uint32_t *K = bsk + (ir * 2u + j) * N;
+    __align__(16) __half row[8];
+    for (uint32_t kap = 0; kap < 8u; ++kap) {
+      const int32_t s = (int32_t)(8u * delta + rho + kap);
+      int32_t v = 0;
+      if (s <= (int32_t)(2u * N - 2u)) {
+        const int32_t x = s - (int32_t)(N - 1u);
+        const uint32_t w = (x >= 0) ? K[x] : (0u - K[x + (int32_t)N]);
+        v = limb8(w, L);
+      }
+      row[kap] = __int2half_rn(v);
+    }
+    *reinterpret_cast<uint4 *>(strips + e * 8u) = *reinterpret_cast<const uint4 *>(row);
+  }
+}
+
+struct TcLut {
+  uint32_t L;
+  const uint32_t *tv;
+  const int32_t *rpos;
+  const int32_t *rval;
+  uint32_t nnz0, nnz1, off0, off1;
+};
+
+struct TcSmem {
+  uint32_t a, b, bars, tmem_slot, total;
+};
+__host__ __device__ inline TcSmem tc_smem(uint32_t N) {
+  TcSmem s;
+  uint32_t o = 0;
+  s.a = o; o += kAStages * kATile;
+  s.b = o; o += 2u * ((kBN + N) / 8u) * 128u;
+  s.bars = o; o += 32u * 8u;
+  s.tmem_slot = o; o += 16u;
+  s.total = o;
+  return s;
+}
+
+// Global scratch of one cluster tile: ACC [128][2][N] u32 then digits
+// [R][N/64 tiles][16 KB].
+__host__ __device__ inline uint64_t tc_tile_acc_words(uint32_t N) { return (uint64_t)kBt * 2u * N; }
+__host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t R) {
+  return (uint64_t)R * (N / kKB) * (kATile / 2);
+}
+
+template <int N>
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
+    k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
+                      const uint32_t *__restrict__ ct_in, size_t count, TcLut lut,
+                      uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
+                      uint32_t chunk_r, uint32_t *__restrict__ big_out, int *status) {
+  constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
+  constexpr uint32_t WIN = (kBN + N) / 8u;   // core matrices in one B window
+  constexpr uint32_t KBLK = N / kKB;         // A tiles per key row r
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const TcSmem S = tc_smem(N);
+  unsigned char *sA = smem + S.a;
+  unsigned char *sB = smem + S.b;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S.bars);
+  uint64_t *a_full = bars, *a_empty = bars + kAStages;
+  uint64_t *b_full = bars + 2 * kAStages, *b_empty = b_full + 2;
+  uint64_t *t_full = b_empty + 2, *t_empty = t_full + 2;
+  volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
+  __shared__ int s_abort;
+
+  const uint32_t n = P.n, l = P.l, R = 2u * l;
+  const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
+  const uint32_t q = cluster_rank();
+  const uint64_t tile = blockIdx.x / kCluster;
+  const size_t base = (size_t)tile * kBt;
+  uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);            // [128][2][N]
+  __half *dig = dig_g + tile * tc_tile_dig_halves(N, R);
+  const uint32_t jq = q / 2u;                 // output polynomial of this CTA
+  const uint32_t cq = (q % 2u) * (N / 2u);    // first output coefficient
+  const uint32_t nblk = (N / 2u) / kBN;       // blocks of 256 per CTA
+  const uint32_t nchunk = R / chunk_r;
+  const uint64_t strip_halves = (uint64_t)(N / 4u) * 64u;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kAStages; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], kCluster); }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1);
+      mbar_init(&t_full[s], 1); mbar_init(&t_empty[s], 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void *)tmem_slot)),
+                 "r"((uint32_t)kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // initial accumulators of this CTA's 32 ciphertexts: (0, X^{-b~} TV)
+  const uint32_t half_delta = P.delta() >> 1;
+  for (uint32_t e = tid; e < 32u * N; e += kThreads) {
+    const uint32_t b = 32u * q + e / N, c = e % N;
+    const uint32_t v_ct = (base + b < count) ? ct_in[(base + b) * (n + 1u) + n] : 0u;
+    const uint32_t bb = fhe::mod_switch_2n(v_ct, LOG2_2N);
+    const uint32_t s = (c + bb) & (2u * N - 1u);
+    uint32_t v;
+    if (lut.L == 1u) v = (s < N) ? lut.tv[s] : (0u - lut.tv[s - N]);
+    else v = (s < N) ? half_delta : (0u - half_delta);
+    acc[((uint64_t)b * 2u + 0u) * N + c] = 0u;
+    acc[((uint64_t)b * 2u + 1u) * N + c] = v;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  cluster_sync_all();
+
+  const uint32_t total_bits = l * P.log2_bg;
+  const uint32_t Bmask = (1u << P.log2_bg) - 1u, Bhalf = 1u << (P.log2_bg - 1u);
+  constexpr uint32_t idesc = idesc_f16(kBt, kBN);
+  // pipeline state (persistent across steps)
+  uint32_t a_it = 0, b_it = 0, u_it = 0;
+
+  for (uint32_t i = 0; i < n; ++i) {
+    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 32 ciphertexts
+    for (uint32_t e = tid; e < 32u * 2u * N; e += kThreads) {
+      const uint32_t c = e % N, j = (e / N) & 1u, b = 32u * q + e / (2u * N);
+      const uint32_t av = (base + b < count) ? ct_in[(base + b) * (n + 1u) + i] : 0u;
+      const uint32_t a = fhe::mod_switch_2n(av, LOG2_2N);
+      const uint32_t *Pj = acc + ((uint64_t)b * 2u + j) * N;
+      const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
+      const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
+      const uint32_t x = rot - Pj[c];
+      uint32_t xr = (total_bits >= 32u) ? x
+                                         : ((uint32_t)(x + (1u << (31u - total_bits))) >> (32u - total_bits));
+      const uint32_t tp = N - 1u - c;  // reversed digit index t'
+      const uint32_t in_tile = (b / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (b % 8u) * 8u + (tp % 8u);
+      for (int lam = (int)l - 1; lam >= 0; --lam) {
+        uint32_t d = xr & Bmask;
+        xr >>= P.log2_bg;
+        int32_t sd = (int32_t)d;
+        if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr += 1u; }
+        const uint32_t r = j * l + (uint32_t)lam;
+        dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(sd);
+      }
+    }
+    asm volatile("fence.proxy.async;" ::: "memory");
+    cluster_sync_all();
+
+    // ---- external product units: (block, limb, chunk)
+    if (warp == 0) {
+      if (lane == 0) {
+        for (uint32_t blk = 0; blk < nblk; ++blk) {
+          const uint32_t c0 = cq + blk * kBN;
+          for (uint32_t L = 0; L < 4u; ++L)
+            for (uint32_t ch = 0; ch < nchunk; ++ch)
+              for (uint32_t rr = 0; rr < chunk_r; ++rr) {
+                const uint32_t r = ch * chunk_r + rr;
+                const uint32_t bs = b_it & 1u;
+                if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
+                if (!s_abort) {
+                  const __half *src = strips + ((((uint64_t)i * R + r) * 2u + jq) * 4u + L) * strip_halves +
+                                      (uint64_t)(c0 / 8u) * 64u;
+                  mbar_expect_tx(&b_full[bs], WIN * 128u);
+                  bulk_g2s(sB + bs * WIN * 128u, src, WIN * 128u, &b_full[bs]);
+                }
+                ++b_it;
+                for (uint32_t kb = 0; kb < KBLK; ++kb) {
+                  const uint32_t as = a_it % kAStages;
+                  if (a_it >= kAStages)
+                    wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
+                  if (!s_abort) {
+                    const __half *src = dig + (uint64_t)(r * KBLK + kb) * (kATile / 2) + q * (kATile / 8);
+                    mbar_expect_tx(&a_full[as], kATile);
+                    bulk_g2s_multicast(sA + as * kATile + q * (kATile / 4), src, kATile / 4,
+                                       &a_full[as], (uint16_t)((1u << kCluster) - 1u));
+                  }
+                  ++a_it;
+                }
+              }
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        for (uint32_t blk = 0; blk < nblk; ++blk)
+          for (uint32_t L = 0; L < 4u; ++L)
+            for (uint32_t ch = 0; ch < nchunk; ++ch) {
+              const uint32_t buf = u_it & 1u;
+              if (u_it >= 2u) wait_bounded(&t_empty[buf], ((u_it >> 1) - 1u) & 1u, &s_abort);
+              tc_fence_after();
+              const uint32_t d_tmem = tmem + buf * (uint32_t)kBN;
+              uint32_t accum = 0;
+              for (uint32_t rr = 0; rr < chunk_r; ++rr) {
+                const uint32_t bs = b_it & 1u;
+                wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort);
+                const uint32_t bbase = smem_u32(sB + bs * WIN * 128u);
+                for (uint32_t kb = 0; kb < KBLK; ++kb) {
+                  const uint32_t as = a_it % kAStages;
+                  wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
+                  tc_fence_after();
+                  if (!s_abort) {
+                    const uint32_t abase = smem_u32(sA + as * kATile);
+#pragma unroll
+                    for (uint32_t s = 0; s < 4u; ++s) {
+                      const uint64_t ad = smem_desc(abase + s * 256u, 128u, 1024u);
+                      const uint64_t bd = smem_desc(bbase + (8u * kb + 2u * s) * 128u, 128u, 128u);
+                      tc_mma_f16(d_tmem, ad, bd, idesc, accum);
+                      accum = 1u;
+                    }
+                    tc_commit_multicast(&a_empty[as], (uint16_t)((1u << kCluster) - 1u));
+                  }
+                  ++a_it;
+                }
+                if (!s_abort) tc_commit(&b_empty[bs]);
+                ++b_it;
+              }
+              if (!s_abort) tc_commit(&t_full[buf]);
+              ++u_it;
+            }
+      }
+      __syncwarp();
+    } else {
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 and columns
+      // 128 * ((w - 2) / 4) .. +128 of each 256-column buffer
+      const uint32_t quarter = warp % 4u, half = (warp - 2u) / 4u;
+      const uint32_t b = 32u * quarter + lane;  // ciphertext row of the tile
+      for (uint32_t blk = 0; blk < nblk; ++blk) {
+        uint32_t outv[128];
+#pragma unroll
+        for (int k = 0; k < 128; ++k) outv[k] = 0u;
+        for (uint32_t L = 0; L < 4u; ++L)
+          for (uint32_t ch = 0; ch < nchunk; ++ch) {
+            const uint32_t buf = u_it & 1u;
+            const bool got = wait_bounded(&t_full[buf], (u_it >> 1) & 1u, &s_abort);
+            const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
+            tc_fence_after();
+            if (ok) {
+              const uint32_t tbase = tmem + ((32u * quarter) << 16) + buf * (uint32_t)kBN + half * 128u;
+#pragma unroll
+              for (uint32_t part = 0; part < 4u; ++part) {
+                uint32_t r[32];
+                tc_ld32(tbase + part * 32u, r);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                  const int32_t v = __float2int_rn(__uint_as_float(r[k]));
+                  outv[part * 32 + k] += (uint32_t)v << (8u * L);
+                }
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[buf]);
+            ++u_it;
+          }
+        if (!__any_sync(0xffffffffu, s_abort != 0)) {
+          const uint32_t c0 = cq + blk * kBN + half * 128u;
+          uint32_t *dst = acc + ((uint64_t)b * 2u + jq) * N + c0;
+#pragma unroll
+          for (int k = 0; k < 128; k += 4) {
+            uint4 v = *reinterpret_cast<uint4 *>(dst + k);
+            v.x += outv[k]; v.y += outv[k + 1]; v.z += outv[k + 2]; v.w += outv[k + 3];
+            *reinterpret_cast<uint4 *>(dst + k) = v;
+          }
+        }
+      }
+    }
+    // keep every warp's iteration counters in step (only the issuing lanes and
+    // the epilogue advanced their own copies)
+    {
+      const uint32_t per_step_r = nblk * 4u * nchunk * chunk_r;
+      const uint32_t a_step = per_step_r * KBLK, u_step = nblk * 4u * nchunk;
+      if (warp == 0) { if (lane != 0) { a_it += a_step; b_it += per_step_r; } u_it += u_step; }
+      else if (warp == 1) { if (lane != 0) { a_it += a_step; b_it += per_step_r; u_it += u_step; } }
+      else { a_it += a_step; b_it += per_step_r; }
+    }
+    cluster_sync_all();
+  }
+
+  // ---- sample extraction (with the multi-value split when L == 2)
+  const uint32_t W = N + 1u;
+  for (uint32_t jl = 0; jl < lut.L; ++jl) {
+    const uint32_t nnz = jl ? lut.nnz1 : lut.nnz0, off = jl ? lut.off1 : lut.off0;
+    for (uint32_t e = tid; e < 32u * W; e += kThreads) {
+      const uint32_t b = 32u * q + e / W, c = e % W;
+      if (base + b >= count) continue;
+      const uint32_t *A = acc + ((uint64_t)b * 2u) * N;
+      const uint32_t *B = acc + ((uint64_t)b * 2u + 1u) * N;
+      uint32_t v;
+      if (lut.L == 1u) {
+        v = (c == N) ? B[0] : (c == 0 ? A[0] : (0u - A[N - c]));
+      } else {
+        const uint32_t m = (c == N || c == 0) ? 0u : N - c;
+        const uint32_t *Pp = (c == N) ? B : A;
+        uint32_t s = 0;
+        for (uint32_t t = 0; t < nnz; ++t) {
+          const uint32_t ep = (uint32_t)lut.rpos[off + t];
+          const uint32_t val = (uint32_t)lut.rval[off + t];
+          s += val * ((m >= ep) ? Pp[m - ep] : (0u - Pp[m + N - ep]));
+        }
+        v = (c == N || c == 0) ? s : (0u - s);
+      }
+      big_out[((size_t)jl * count + base + b) * W + c] = v;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)kTmemCols));
+  }
+  if (tid == 0 && s_abort) atomicExch(status, FHE_ETIMEOUT);
+}
+
+}  // namespace
+
 namespace fhe {
+
+// Largest number of key rows r per fp32 accumulation that keeps every partial
+// sum within 2^24: (Bg/2) * 128 * chunk_r * N <= 2^24.
+static uint32_t tc_chunk_r(const Params &P) {
+  const uint64_t per_r = (uint64_t)(1u << (P.log2_bg - 1u)) * 128u * P.N;
+  uint32_t cr = 0;
+  while ((uint64_t)(cr + 1u) * per_r <= (1ull << 24) && cr + 1u <= P.rows()) ++cr;
+  while (cr > 0 && P.rows() % cr) --cr;
+  return cr;
+}
+
+static bool tc_supported(const Params &P) {
+  return P.k == 1u && P.N == 1024u && tc_chunk_r(P) >= 1u;
+}
+
+int tc_prepare(fhe_keys *K) {
+  const Params &P = K->P;
+  if (K->d_bsk_tc && K->d_acc_tc && K->d_digits_tc) return FHE_OK;
+  const uint64_t strips = (uint64_t)P.n * P.rows() * 2u * 4u;
+  K->bsk_tc_bytes = strips * (P.N / 4u) * 128u;
+  const uint64_t tiles = (K->ws_cap + kBt - 1) / kBt;
+  if (cudaMalloc(&K->d_bsk_tc, K->bsk_tc_bytes) != cudaSuccess) return FHE_ENOMEM;
+  if (cudaMalloc(&K->d_acc_tc, sizeof(uint32_t) * tiles * tc_tile_acc_words(P.N)) != cudaSuccess)
+    return FHE_ENOMEM;
+  if (cudaMalloc(&K->d_digits_tc, sizeof(__half) * tiles * tc_tile_dig_halves(P.N, P.rows())) !=
+      cudaSuccess)
+    return FHE_ENOMEM;
+  k_hankel_strips<<<152u * 16u, 256>>>(P, K->d_bsk, (__half *)K->d_bsk_tc);
+  note_launches(1);
+  FHE_CUDA_TRY(cudaGetLastError());
+  FHE_CUDA_TRY(cudaDeviceSynchronize());
+  return FHE_OK;
+}
+
+int pbs_prepare(fhe_keys *K, int variant) {
+  if (variant != FHE_VARIANT_TC) return FHE_OK;
+  if (!tc_supported(K->P)) return FHE_EUNSUPPORTED;
+  return tc_prepare(K);
+}
+
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
            uint32_t *ct_out, cudaStream_t st) {
-  (void)K; (void)ct_in; (void)count; (void)lut; (void)ct_out; (void)st;
-  return FHE_EUNSUPPORTED;
+  const Params &P = K->P;
+  if (!tc_supported(P)) return FHE_EUNSUPPORTED;
+  int rc = tc_prepare(K);
+  if (rc) return rc;
+  TcLut la;
+  la.L = lut->L;
+  la.tv = lut->d_tv;
+  la.rpos = lut->d_rpos;
+  la.rval = lut->d_rval;
+  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
+  la.off0 = lut->off[0]; la.off1 = lut->off[1];
+  const uint32_t chunk_r = tc_chunk_r(P);
+  const TcSmem S = tc_smem(P.N);
+  auto kern = k_blind_rotate_tc<1024>;
+  FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
+    const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
+    const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
+    const bool prof = (s0 == 0) && K->prof_ev0;
+    if (prof) { FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev0, st, cudaEventRecordExternal)); K->prof_count = cnt; }
+    kern<<<tiles * kCluster, kThreads, S.total, st>>>(
+        P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
+        (__half *)K->d_digits_tc, chunk_r, K->d_big, K->d_status);
+    note_launches(1);
+    FHE_CUDA_TRY(cudaGetLastError());
+    if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
+    for (uint32_t j = 0; j < lut->L; ++j) {
+      rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
+                            ct_out + ((size_t)j * count + s0) * (P.n + 1u), st);
+      if (rc) return rc;
+    }
+  }
+  return FHE_OK;
 }
+
 }  // namespace fhe

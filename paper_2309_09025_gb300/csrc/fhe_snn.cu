@@ -89,7 +89,9 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
     f[u] = (v >= d->v_th) ? d->spike_scale : 0;
     f[p + u] = (v >= d->v_th) ? 0 : (v >= 0 ? (v >> d->leak_shift) : 0);
   }
-  int rc = fhe_lut_create(K, f.data(), 2u, &S->lut);
+  int rc = fhe::pbs_prepare(K, d->variant);
+  if (rc) { snn_release(S); return rc; }
+  rc = fhe_lut_create(K, f.data(), 2u, &S->lut);
   if (rc) { snn_release(S); return rc; }
   uint32_t prev = 0;
   const uint32_t W = P.n + 1u;

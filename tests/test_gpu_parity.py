@@ -101,7 +101,18 @@ def _luts(P, L):
     return O.lif_luts(P, v_th=8 if p >= 32 else 2, leak_shift=1, spike_scale=1)
 
 
-VARIANTS = ["EXACT"]
+VARIANTS = ["EXACT", "TC"]
+
+
+def pbs(fhe, K, ct, lut, variant):
+    """pbs_batch through the C ABI; variants without coverage of a parameter
+    set (FHE_EUNSUPPORTED) are skipped, never replaced."""
+    try:
+        return fhe.pbs_batch(K, ct, lut, getattr(fhe, "VARIANT_" + variant))
+    except fhe.FheError as e:
+        if e.code == fhe.FHE_EUNSUPPORTED:
+            pytest.skip("%s variant does not cover this parameter set" % variant)
+        raise
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -114,7 +125,7 @@ def test_pbs_p64_bit_exact_all_messages(fhe, oracle_keys, variant, L):
     ct = O.encrypt(P, OK, m, 123)  # 101 ciphertexts: ragged against 8 per CTA
     luts = _luts(P, L)
     lut = fhe.lut_create(K, luts)
-    out = fhe.pbs_batch(K, ct, lut, getattr(fhe, "VARIANT_" + variant))
+    out = pbs(fhe, K, ct, lut, variant)
     torch.cuda.synchronize()
     ref = O.pbs(P, OK, ct, luts, nthreads=NTHREADS)
     assert np.array_equal(u32(out), ref)
@@ -130,7 +141,7 @@ def test_pbs_t0_brute_force_and_bit_exact(fhe, oracle_keys, variant):
     ct = O.encrypt(P, OK, m, 5)
     for L in (1, 2):
         luts = _luts(P, L)
-        out = fhe.pbs_batch(K, ct, fhe.lut_create(K, luts), getattr(fhe, "VARIANT_" + variant))
+        out = pbs(fhe, K, ct, fhe.lut_create(K, luts), variant)
         got = u32(out)
         for j in range(L):
             dec = O.decrypt(P, OK, got[j])
@@ -170,7 +181,7 @@ def test_pbs_full_size_sampled(fhe, oracle_keys, name, count, variant):
     m = synth.uniform_messages(31, count, p)
     ct = fhe.encrypt(K, m, seed=99)
     luts = _luts(P, 1)
-    out = fhe.pbs_batch(K, ct, fhe.lut_create(K, luts), getattr(fhe, "VARIANT_" + variant))
+    out = pbs(fhe, K, ct, fhe.lut_create(K, luts), variant)
     got = u32(out)[0]
     octs = O.encrypt(P, OK, m, 99)
     assert np.array_equal(u32(ct), octs)
@@ -222,3 +233,45 @@ def test_snn_csnn_topology_small_params_bit_exact(fhe, oracle_keys):
     for i in range(2):
         ref = O.snn_encrypted(P, OK, net, ct[i], nthreads=NTHREADS)
         assert np.array_equal(scores[i], ref["scores"])
+
+
+def test_tc_matches_exact_full_batch_p630(fhe, oracle_keys):
+    """Tensor-core blind rotation: every output of a multi-cluster P630 batch
+    (ragged against 128-ciphertext tiles) bit-identical to the CUDA-core path,
+    sampled outputs bit-identical to the oracle, for both table counts."""
+    P, K = gpu_keys(fhe, "P630", 3)
+    _, OK = oracle_keys("P630", 3)
+    p = 1 << P["log2_p"]
+    count = 389
+    m = synth.uniform_messages(41, count, p)
+    ct = fhe.encrypt(K, m, seed=7)
+    for L in (1, 2):
+        luts = _luts(P, L)
+        lut = fhe.lut_create(K, luts)
+        ref_gpu = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
+        got = u32(pbs(fhe, K, ct, lut, "TC"))
+        assert np.array_equal(got, ref_gpu)
+        idx = np.array([0, 127, 128, count - 1])
+        ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
+        assert np.array_equal(got[:, idx], ref)
+    assert K.status() == fhe.FHE_OK
+
+
+def test_snn_toy_layer_tc_bit_exact(fhe, oracle_keys):
+    """Encrypted LIF layer on the tensor-core path (low-noise ring N=1024)."""
+    P, K = gpu_keys(fhe, "T0", 2)
+    _, OK = oracle_keys("T0", 2)
+    net = synth.toy_lif_net(seed=4)
+    net["lif"] = dict(v_th=3, leak_shift=1, spike_scale=1)
+    x = synth.bernoulli_spikes(5, 2, 16, 0.3)
+    ct = O.encrypt(P, OK, x.reshape(-1), 9).reshape(2, 1, 16, -1)
+    try:
+        snn = fhe.Snn(K, net, max_images=1, variant=fhe.VARIANT_TC, use_graph=True)
+    except fhe.FheError as e:
+        if e.code == fhe.FHE_EUNSUPPORTED:
+            pytest.skip("TC variant does not cover this parameter set")
+        raise
+    scores = torch.empty((1, 32, P["n"] + 1), dtype=torch.int32, device="cuda")
+    snn.infer(torch.from_numpy(ct.view(np.int32)).cuda(), 1, scores)
+    ref = O.snn_encrypted(P, OK, net, ct[:, 0], nthreads=NTHREADS)
+    assert np.array_equal(u32(scores)[0], ref["scores"])
