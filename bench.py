@@ -36,6 +36,11 @@ SM_COUNT = 152
 # INT32 multiply-add issue rate of one SM (4 SMSPs x 16 lanes per clock).
 IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one blind-rotation launch,
+# from the ncu captures summarised in profiles/blind_rotate_*_p630.md (the key
+# layout is read once per launch from DRAM, so the figure does not scale with
+# the batch).  Set to None whenever the kernel changes until re-captured.
+TRAFFIC_BYTES = {"tc": 1.016512e9 + 8.411648e6, "exact": 34.066688e6 + 16.64e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 
 
@@ -275,7 +280,7 @@ def run_ours(args):
         achieved = macs_per_launch / (br_avg_ms / 1e3) / 1e12
         peak = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES["exact"],
                 "kernel": "k_blind_rotate_exact<1024,4>",
                 "peak_basis": "152 SMs x 64 INT32 multiply-adds/clk x 2070 MHz (derived)"}
     else:
@@ -284,7 +289,8 @@ def run_ours(args):
         achieved = flops / (br_avg_ms / 1e3) / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "blind rotation (tcgen05)",
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES["tc"],
+                "kernel": "k_blind_rotate_tc<1024>",
                 "peak_basis": "measured bf16 sustained (fp16 same rate), of measured"}
     roof["launch_ms"] = br_avg_ms
     roof["launches"] = br_launches
