@@ -163,6 +163,30 @@ void fhe_lut_free(fhe_lut *lut);
 int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                   uint32_t *ct_out, int variant, void *stream);
 
+/* Bootstrapping that allocates nothing (no counterpart in the paper: an
+ * integration aid).  Some callers cannot call cudaMalloc at the point where
+ * they bootstrap: a host framework that owns the whole device memory budget
+ * through its own allocator, or a latency-critical serving loop where an
+ * allocation (which can synchronize the device or fail under memory pressure)
+ * is not acceptable.  This call computes exactly what fhe_pbs_batch computes
+ * with FHE_VARIANT_EXACT (bit-identical outputs, same argument layouts), but
+ * keeps its intermediate ciphertexts in one fixed scratch array compiled into
+ * the library (FHE_PBS_NOALLOC_MAX_WORDS 32-bit words = 4 MiB, held by every
+ * GPU that loads the library until the process exits) instead of the key
+ * handle's workspace.  The caller still provides inputs, outputs, keys and
+ * table, created beforehand.
+ * Limit: L * count * (k*N + 1) <= FHE_PBS_NOALLOC_MAX_WORDS, e.g. count <= 511
+ * for two tables at N = 1024; larger batches return FHE_EINVAL (split them).
+ * The first call on a device resolves the scratch address on that device
+ * (make that first call before any stream capture).  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialized by the caller.
+ * Errors: FHE_EINVAL (bad argument, batch above the limit, keys of another
+ * device), FHE_ECUDA. */
+#define FHE_PBS_NOALLOC_MAX_WORDS (1u << 20)
+int fhe_pbs_batch_noalloc(const fhe_keys *keys, const uint32_t *ct_in, size_t count,
+                          const fhe_lut *lut, uint32_t *ct_out, void *stream);
+
 /* Device status word: FHE_OK, or FHE_ETIMEOUT if a bounded device wait gave
  * up since the last call.  Synchronizes `stream`, then clears the word. */
 int fhe_status(fhe_keys *keys, void *stream);

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfhe_dicsnn.so")
-SOURCES = ["fhe_keys.cu", "fhe_linear.cu", "fhe_pbs_exact.cu", "fhe_pbs_tc.cu", "fhe_snn.cu"]
+SOURCES = ["fhe_keys.cu", "fhe_linear.cu", "fhe_pbs_exact.cu", "fhe_pbs_tc.cu", "fhe_snn.cu",
+           "fhe_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -152,6 +152,10 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
               uint32_t *ct_out, cudaStream_t st);
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
            uint32_t *ct_out, cudaStream_t st);
+// Exact bootstrapping with the extracted ciphertexts in a caller buffer
+// (fhe_noalloc.cu); single batch, no allocation.
+int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+                   uint32_t *ct_out, uint32_t *big, cudaStream_t st);
 // Builds the variant's key layout and workspace ahead of the first call
 // (FHE_OK for variants without one; FHE_EUNSUPPORTED for unsupported sets).
 int pbs_prepare(fhe_keys *K, int variant);

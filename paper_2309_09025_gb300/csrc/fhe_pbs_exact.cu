@@ -428,6 +428,36 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
   return FHE_OK;
 }
 
+// Exact bootstrapping of one batch whose extracted LWE_z ciphertexts go to the
+// caller-provided device buffer `big` ([L][count][kN+1] words); no
+// workspace of the key handle is touched and nothing is allocated.
+int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+                   uint32_t *ct_out, uint32_t *big, cudaStream_t st) {
+  const Params &P = K->P;
+  LutArgs la;
+  la.L = lut->L;
+  la.tv = lut->d_tv;
+  la.rpos = lut->d_rpos;
+  la.rval = lut->d_rval;
+  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
+  la.off0 = lut->off[0]; la.off1 = lut->off[1];
+  int rc;
+  switch (P.N) {
+    case 256: rc = launch_br<256, 8>(K, ct_in, count, la, big, st); break;
+    case 512: rc = launch_br<512, 8>(K, ct_in, count, la, big, st); break;
+    case 1024: rc = launch_br<1024, 4>(K, ct_in, count, la, big, st); break;
+    case 2048: rc = launch_br<2048, 2>(K, ct_in, count, la, big, st); break;
+    default: return FHE_EUNSUPPORTED;
+  }
+  if (rc) return rc;
+  for (uint32_t j = 0; j < lut->L; ++j) {
+    rc = key_switch_batch(K, big + (size_t)j * count * P.big_words(), count,
+                          ct_out + (size_t)j * count * (P.n + 1u), st);
+    if (rc) return rc;
+  }
+  return FHE_OK;
+}
+
 }  // namespace fhe
 
 extern "C" int fhe_pbs_batch(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,

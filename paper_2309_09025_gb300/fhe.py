@@ -33,7 +33,9 @@ EXPORTED = (
     "fhe_lwe_conv2d", "fhe_lut_create", "fhe_lut_free", "fhe_pbs_batch", "fhe_status",
     "fhe_snn_create", "fhe_snn_free", "fhe_snn_pbs_per_image", "fhe_snn_infer",
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
+    "fhe_pbs_batch_noalloc",
 )
+PBS_NOALLOC_MAX_WORDS = 1 << 20
 
 
 class FheError(RuntimeError):
@@ -110,6 +112,7 @@ def lib():
             "fhe_snn_profile": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(u64), ctypes.POINTER(u64)]),
             "fhe_kernel_launches": (u64, []),
+            "fhe_pbs_batch_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -278,6 +281,20 @@ def pbs_batch(keys, ct_in, lut, variant=VARIANT_EXACT, out=None, stream=None):
         out = torch.empty((lut.L, count, w), dtype=torch.int32, device="cuda")
     _check(lib().fhe_pbs_batch(keys.handle, _ptr(ct_in), count, lut.handle, _ptr(out),
                                int(variant), _stream(stream)), "pbs_batch")
+    return out
+
+
+def pbs_batch_noalloc(keys, ct_in, lut, out=None, stream=None):
+    """fhe_pbs_batch_noalloc: exact bootstrapping with the library's fixed
+    scratch array (no allocation in the library); (L, count, n+1) int32."""
+    import torch
+    w = keys.params["n"] + 1
+    ct_in = _dev_u32(ct_in)
+    count = ct_in.numel() // w
+    if out is None:
+        out = torch.empty((lut.L, count, w), dtype=torch.int32, device="cuda")
+    _check(lib().fhe_pbs_batch_noalloc(keys.handle, _ptr(ct_in), count, lut.handle, _ptr(out),
+                                       _stream(stream)), "pbs_batch_noalloc")
     return out
 
 
