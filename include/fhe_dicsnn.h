@@ -247,6 +247,22 @@ uint64_t fhe_snn_pbs_per_image(const fhe_snn *net);
 int fhe_snn_infer(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
                   int inputs_on_host, void *stream);
 
+/* The same inference split into its steps (fhe_snn_infer = begin, step until
+ * it returns 0, end).  Layer-skewed schedule: step tau advances every layer l
+ * whose time step t = tau - l lies in [0, T) -- layer l at t needs only layer
+ * l-1 at t and itself at t-1 (Thm 3.2 recurrence) -- so one bootstrap launch
+ * serves all active layers; an inference is T + n_layers - 1 steps.
+ * begin: stages the input (layouts as in fhe_snn_infer) and resets the state.
+ * step:  enqueues the next step (its CUDA graph when use_graph bit 0 is set);
+ *        returns the number of steps still to run (>= 0) or an FHE_E* code.
+ * end:   copies the encrypted scores out (synchronizing when on host). */
+int fhe_snn_begin(fhe_snn *net, const uint32_t *ct_input, size_t n_images, int inputs_on_host,
+                  void *stream);
+int fhe_snn_step(fhe_snn *net, void *stream);
+int fhe_snn_end(fhe_snn *net, uint32_t *scores, int inputs_on_host, void *stream);
+/* Number of steps of one inference (T + n_layers - 1). */
+uint32_t fhe_snn_iterations(const fhe_snn *net);
+
 /* Optional: device spike ciphertexts of layer `layer` at the last step of
  * the last inference, copied to device buffer dst [n_images][size][n+1]. */
 int fhe_snn_layer_spikes(const fhe_snn *net, uint32_t layer, uint32_t *dst, void *stream);

@@ -148,10 +148,14 @@ namespace fhe {
 void note_launches(int64_t n);
 uint64_t launches();
 // Implemented in fhe_pbs_exact.cu / fhe_pbs_tc.cu.
+// Table j of the outputs starts at ct_out + j * table_stride (words).
 int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-              uint32_t *ct_out, cudaStream_t st);
+              uint32_t *ct_out, size_t table_stride, cudaStream_t st);
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-           uint32_t *ct_out, cudaStream_t st);
+           uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+// Dispatch on the variant (FHE_EINVAL for an unknown one).
+int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st);
 // Exact bootstrapping with the extracted ciphertexts in a caller buffer
 // (fhe_noalloc.cu); single batch, no allocation.
 int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,

@@ -395,7 +395,7 @@ int key_switch_batch(const fhe_keys *K, const uint32_t *d_big, size_t count, uin
 }
 
 int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-              uint32_t *ct_out, cudaStream_t st) {
+              uint32_t *ct_out, size_t table_stride, cudaStream_t st) {
   const Params &P = K->P;
   LutArgs la;
   la.L = lut->L;
@@ -421,7 +421,7 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
     if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
     for (uint32_t j = 0; j < lut->L; ++j) {
       rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
-                            ct_out + ((size_t)j * count + s0) * (P.n + 1u), st);
+                            ct_out + (size_t)j * table_stride + s0 * (P.n + 1u), st);
       if (rc) return rc;
     }
   }
@@ -458,6 +458,14 @@ int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const
   return FHE_OK;
 }
 
+int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st) {
+  if (!count) return FHE_OK;
+  if (variant == FHE_VARIANT_EXACT) return pbs_exact(K, ct_in, count, lut, ct_out, table_stride, st);
+  if (variant == FHE_VARIANT_TC) return pbs_tc(K, ct_in, count, lut, ct_out, table_stride, st);
+  return FHE_EINVAL;
+}
+
 }  // namespace fhe
 
 extern "C" int fhe_pbs_batch(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
@@ -465,7 +473,5 @@ extern "C" int fhe_pbs_batch(fhe_keys *K, const uint32_t *ct_in, size_t count, c
   if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N) return FHE_EINVAL;
   if (!count) return FHE_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (variant == FHE_VARIANT_EXACT) return fhe::pbs_exact(K, ct_in, count, lut, ct_out, st);
-  if (variant == FHE_VARIANT_TC) return fhe::pbs_tc(K, ct_in, count, lut, ct_out, st);
-  return FHE_EINVAL;
+  return fhe::pbs_run(K, ct_in, count, lut, ct_out, count * (K->P.n + 1u), variant, st);
 }

@@ -47,7 +47,7 @@ constexpr int kCluster = 4;
 constexpr int kBt = 128;          // ciphertexts per cluster (MMA M)
 constexpr int kBN = 256;          // output coefficients per block (MMA N)
 constexpr int kKB = 64;           // K elements per A tile
-constexpr int kAStages = 6;
+constexpr int kAStages = 10;
 constexpr int kATile = kBt * kKB * 2;   // 16 KB
 constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
 constexpr int kTmemCols = 512;
@@ -313,30 +313,57 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t a_it = 0, b_it = 0, u_it = 0;
 
   for (uint32_t i = 0; i < n; ++i) {
-    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 32 ciphertexts
-    for (uint32_t e = tid; e < 32u * 2u * N; e += kThreads) {
-      const uint32_t c = e % N, j = (e / N) & 1u, b = 32u * q + e / (2u * N);
-      const uint32_t av = (base + b < count) ? ct_in[(base + b) * (n + 1u) + i] : 0u;
+    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 32 ciphertexts.
+    // A group = 8 consecutive coefficients c0..c0+7 of one polynomial: their
+    // reversed indices t' = N-1-c form exactly one 8-element core-matrix row,
+    // so each gadget level is one 16-byte store.
+    for (uint32_t grp = tid; grp < 32u * 2u * (N / 8u); grp += kThreads) {
+      const uint32_t c0 = (grp % (N / 8u)) * 8u;
+      const uint32_t j = (grp / (N / 8u)) & 1u;
+      const uint32_t b = 32u * q + grp / (2u * (N / 8u));
+      const uint32_t av = (base + b < count) ? __ldg(ct_in + (base + b) * (n + 1u) + i) : 0u;
       const uint32_t a = fhe::mod_switch_2n(av, LOG2_2N);
       const uint32_t *Pj = acc + ((uint64_t)b * 2u + j) * N;
-      const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
-      const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
-      const uint32_t x = rot - Pj[c];
-      uint32_t xr = (total_bits >= 32u) ? x
-                                         : ((uint32_t)(x + (1u << (31u - total_bits))) >> (32u - total_bits));
-      const uint32_t tp = N - 1u - c;  // reversed digit index t'
-      const uint32_t in_tile = (b / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (b % 8u) * 8u + (tp % 8u);
+      uint32_t own[8], rot[8];
+      const uint4 o0 = *reinterpret_cast<const uint4 *>(Pj + c0);
+      const uint4 o1 = *reinterpret_cast<const uint4 *>(Pj + c0 + 4u);
+      own[0] = o0.x; own[1] = o0.y; own[2] = o0.z; own[3] = o0.w;
+      own[4] = o1.x; own[5] = o1.y; own[6] = o1.z; own[7] = o1.w;
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const uint32_t s = (c0 + k + 2u * N - a) & (2u * N - 1u);
+        rot[k] = (s < N) ? Pj[s] : (0u - Pj[s - N]);
+      }
+      uint32_t xr[8];
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const uint32_t x = rot[k] - own[k];
+        xr[k] = (total_bits >= 32u)
+                    ? x
+                    : ((uint32_t)(x + (1u << (31u - total_bits))) >> (32u - total_bits));
+      }
+      const uint32_t tp0 = N - 8u - c0;  // smallest t' of the group
+      const uint32_t in_tile = (b / 8u) * 512u + ((tp0 % 64u) / 8u) * 64u + (b % 8u) * 8u;
+      // least significant level first (carries propagate upwards)
       for (int lam = (int)l - 1; lam >= 0; --lam) {
-        uint32_t d = xr & Bmask;
-        xr >>= P.log2_bg;
-        int32_t sd = (int32_t)d;
-        if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr += 1u; }
+        __align__(16) __half row[8];  // t' = N-1-(c0+k) sits at position 7-k
+#pragma unroll
+        for (uint32_t k = 0; k < 8u; ++k) {
+          const uint32_t d = xr[k] & Bmask;
+          xr[k] >>= P.log2_bg;
+          int32_t sd = (int32_t)d;
+          if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
+          row[7u - k] = __int2half_rn(sd);
+        }
         const uint32_t r = j * l + (uint32_t)lam;
-        dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(sd);
+        *reinterpret_cast<uint4 *>(dig + (uint64_t)(r * KBLK + tp0 / 64u) * (kATile / 2) + in_tile) =
+            *reinterpret_cast<const uint4 *>(row);
       }
     }
+    // The digits this CTA multicasts are the ones it just wrote (rows 32q..);
+    // a CTA-wide barrier orders them before its producer's bulk copies.
     asm volatile("fence.proxy.async;" ::: "memory");
-    cluster_sync_all();
+    __syncthreads();
 
     // ---- external product units: (block, limb, chunk)
     if (warp == 0) {
@@ -548,7 +575,7 @@ int pbs_prepare(fhe_keys *K, int variant) {
 }
 
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-           uint32_t *ct_out, cudaStream_t st) {
+           uint32_t *ct_out, size_t table_stride, cudaStream_t st) {
   const Params &P = K->P;
   if (!tc_supported(P)) return FHE_EUNSUPPORTED;
   int rc = tc_prepare(K);
@@ -577,7 +604,7 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
     if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
     for (uint32_t j = 0; j < lut->L; ++j) {
       rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
-                            ct_out + ((size_t)j * count + s0) * (P.n + 1u), st);
+                            ct_out + (size_t)j * table_stride + s0 * (P.n + 1u), st);
       if (rc) return rc;
     }
   }

@@ -1,10 +1,16 @@
 // fhe_snn.cu -- encrypted DiCSNN inference (paper 3.1-3.3 network, 4.1
 // WeightSum, 4.2 FHE-Fire / FHE-Reset, 5.3 client/server flow).
 //
-// Per time step and layer:  I = WeightSum(x);  H = V + I + (p/2) Delta;
-// (S, V) = bootstrap(H) with the Fire and Reset tables from ONE blind
-// rotation (multi-value split);  x_next = S;  scores += S of the last layer.
-// Each time step is captured once as a CUDA graph per batch size and replayed.
+// Per layer l and time step t:  I = WeightSum(x);  H = V + I + (p/2) Delta;
+// (S, V) = bootstrap(H) with the Fire and Reset tables from ONE blind rotation
+// (multi-value split);  x_next = S;  scores += S of the last layer.
+//
+// Layer-skewed schedule.  Layer l at step t only needs layer l-1 at step t
+// and itself at step t-1, so iteration tau runs every layer l with
+// t = tau - l in [0, T): all active layers' neurons (of all images) go through
+// ONE bootstrap launch per iteration, T + layers - 1 iterations in total,
+// instead of one mostly-empty launch per layer and step.  Each iteration is
+// captured once as a CUDA graph per batch size and replayed.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -24,9 +30,7 @@ struct Layer {
   int32_t *d_w;
   uint32_t in_size, out_size;
   uint32_t cin, h, w, cout, kh, kw, stride, pad;
-  uint32_t *d_I;    // [max_images][out][n+1]
-  uint32_t *d_H;    // [max_images][out][n+1]
-  uint32_t *d_out;  // [2][max_images * out][n+1]: spikes then membrane V
+  uint32_t *d_I;  // [max_images][out][n+1]
 };
 }  // namespace
 
@@ -36,10 +40,16 @@ struct fhe_snn {
   std::vector<Layer> layers;
   fhe_lut *lut;
   uint32_t n_in, n_out;
+  uint64_t neurons;    // sum of the layers' sizes (per image)
+  uint32_t *d_H;       // bootstrap inputs, all layers: [max_images * neurons][n+1]
+  uint32_t *d_out;     // [2][max_images * neurons][n+1]: spikes, then membrane V
   uint32_t *d_input;   // staging copy of the caller's input
   uint32_t *d_scores;  // [max_images][n_out][n+1]
+  // inference in progress
+  size_t cur_images;
+  uint32_t next_iter;
   size_t graph_images;
-  std::vector<cudaGraphExec_t> graphs;  // one per time step
+  std::vector<cudaGraphExec_t> graphs;  // one per iteration
   std::vector<int64_t> graph_kernels;   // kernel nodes of each graph
   // Graphs are captured and replayed on a library-owned non-blocking stream
   // (the legacy default stream cannot be captured), joined to the caller's
@@ -47,11 +57,15 @@ struct fhe_snn {
   cudaStream_t gs;
   cudaEvent_t join_in, join_out;
   size_t last_images;
-  // instrumentation: one event pair per (step, layer) blind rotation
+  // instrumentation: one event pair per iteration's bootstrap launch
   bool profile;
-  std::vector<cudaEvent_t> ev;  // [T][layers][2]
-  std::vector<size_t> ev_count; // ciphertexts of each bracketed launch
+  std::vector<cudaEvent_t> ev;   // [iterations][2]
+  std::vector<size_t> ev_count;  // ciphertexts of each bracketed launch
 };
+
+static uint32_t snn_iterations(const fhe_snn *S) {
+  return S->desc.T + (uint32_t)S->layers.size() - 1u;
+}
 
 static void snn_release(fhe_snn *S) {
   if (!S) return;
@@ -63,8 +77,11 @@ static void snn_release(fhe_snn *S) {
   if (S->join_out) cudaEventDestroy(S->join_out);
   if (S->gs) cudaStreamDestroy(S->gs);
   for (auto &L : S->layers) {
-    cudaFree(L.d_w); cudaFree(L.d_I); cudaFree(L.d_H); cudaFree(L.d_out);
+    cudaFree(L.d_w);
+    cudaFree(L.d_I);
   }
+  cudaFree(S->d_H);
+  cudaFree(S->d_out);
   cudaFree(S->d_input);
   cudaFree(S->d_scores);
   fhe_lut_free(S->lut);
@@ -122,11 +139,10 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
       S->layers.push_back(L); snn_release(S); return FHE_EINVAL;
     }
     prev = L.out_size;
+    S->neurons += L.out_size;
     const size_t cts = (size_t)d->max_images * L.out_size;
     bool ok = cudaMalloc(&L.d_w, sizeof(int32_t) * wcount) == cudaSuccess &&
-              cudaMalloc(&L.d_I, sizeof(uint32_t) * cts * W) == cudaSuccess &&
-              cudaMalloc(&L.d_H, sizeof(uint32_t) * cts * W) == cudaSuccess &&
-              cudaMalloc(&L.d_out, sizeof(uint32_t) * 2u * cts * W) == cudaSuccess;
+              cudaMalloc(&L.d_I, sizeof(uint32_t) * cts * W) == cudaSuccess;
     S->layers.push_back(L);
     if (!ok) { snn_release(S); return FHE_ENOMEM; }
     if (cudaMemcpy(L.d_w, ld.weights, sizeof(int32_t) * wcount, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -135,8 +151,11 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   }
   S->n_in = S->layers.front().in_size;
   S->n_out = S->layers.back().out_size;
+  const size_t all = (size_t)d->max_images * S->neurons;
   const size_t in_words = (size_t)d->max_images * (d->static_input ? 1u : d->T) * S->n_in * W;
-  if (cudaMalloc(&S->d_input, sizeof(uint32_t) * in_words) != cudaSuccess ||
+  if (cudaMalloc(&S->d_H, sizeof(uint32_t) * all * W) != cudaSuccess ||
+      cudaMalloc(&S->d_out, sizeof(uint32_t) * 2u * all * W) != cudaSuccess ||
+      cudaMalloc(&S->d_input, sizeof(uint32_t) * in_words) != cudaSuccess ||
       cudaMalloc(&S->d_scores, sizeof(uint32_t) * (size_t)d->max_images * S->n_out * W) != cudaSuccess) {
     snn_release(S); return FHE_ENOMEM;
   }
@@ -147,14 +166,27 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   }
   S->profile = (d->use_graph & FHE_SNN_PROFILE) != 0;
   if (S->profile) {
-    S->ev.assign((size_t)d->T * S->layers.size() * 2u, (cudaEvent_t)0);
-    S->ev_count.assign((size_t)d->T * S->layers.size(), 0);
+    S->ev.assign((size_t)snn_iterations(S) * 2u, (cudaEvent_t)0);
+    S->ev_count.assign(snn_iterations(S), 0);
     for (auto &e : S->ev)
       if (cudaEventCreate(&e) != cudaSuccess) { snn_release(S); return FHE_ECUDA; }
   }
   *out = S;
   return FHE_OK;
 }
+
+extern "C" void fhe_snn_free(fhe_snn *S) {
+  if (!S) return;
+  cudaDeviceSynchronize();
+  snn_release(S);
+}
+
+extern "C" uint64_t fhe_snn_pbs_per_image(const fhe_snn *S) {
+  if (!S) return 0;
+  return S->neurons * S->desc.T;
+}
+
+extern "C" uint32_t fhe_snn_iterations(const fhe_snn *S) { return S ? snn_iterations(S) : 0u; }
 
 extern "C" int fhe_snn_profile(const fhe_snn *S, double *br_ms, uint64_t *br_launches,
                                uint64_t *br_ciphertexts) {
@@ -176,77 +208,86 @@ extern "C" int fhe_snn_profile(const fhe_snn *S, double *br_ms, uint64_t *br_lau
   return FHE_OK;
 }
 
-extern "C" void fhe_snn_free(fhe_snn *S) {
-  if (!S) return;
-  cudaDeviceSynchronize();
-  snn_release(S);
-}
-
-extern "C" uint64_t fhe_snn_pbs_per_image(const fhe_snn *S) {
-  if (!S) return 0;
-  uint64_t per_step = 0;
-  for (const auto &L : S->layers) per_step += L.out_size;
-  return per_step * S->desc.T;
-}
-
-// Enqueue one time step t for `ni` images.
-static int snn_step(fhe_snn *S, uint32_t t, size_t ni, cudaStream_t st) {
+// Enqueue iteration tau for `ni` images: every layer l with t = tau - l in
+// [0, T) advances one step; their bootstraps share one launch.
+static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
   const fhe::Params &P = S->K->P;
   const uint32_t W = P.n + 1u;
   const uint32_t half_p = P.delta() * (P.p() / 2u);  // (p/2) * Delta
-  const uint32_t *x = S->d_input + (S->desc.static_input ? 0 : (size_t)t * ni * S->n_in * W);
+  const uint32_t T = S->desc.T, nl = (uint32_t)S->layers.size();
+  const uint32_t lo = (tau >= T) ? tau - T + 1u : 0u;
+  const uint32_t hi = (tau < nl - 1u) ? tau : nl - 1u;
+  const size_t all = ni * S->neurons;
+  uint32_t *spk = S->d_out, *mem = S->d_out + all * W;
+  // segment offsets of the layers (ciphertexts) for this batch size
+  std::vector<size_t> off(nl + 1u, 0);
+  for (uint32_t l = 0; l < nl; ++l) off[l + 1] = off[l] + ni * S->layers[l].out_size;
   int rc;
-  for (size_t li = 0; li < S->layers.size(); ++li) {
-    Layer &L = S->layers[li];
-    const size_t cts = ni * L.out_size;
-    const bool static_first = (li == 0 && S->desc.static_input);
-    if (!(static_first && t > 0)) {
-      if (L.type == FHE_LAYER_FC)
-        rc = fhe_lwe_linear(P.n, P.log2_p, L.d_w, L.out_size, L.in_size, NULL, x, ni, L.d_I, st);
-      else
-        rc = fhe_lwe_conv2d(P.n, P.log2_p, L.d_w, L.cin, L.h, L.w, L.cout, L.kh, L.kw, L.stride,
-                            L.pad, NULL, x, ni, L.d_I, st);
-      if (rc) return rc;
-    }
-    uint32_t *V = L.d_out + cts * W;  // membrane potentials from the previous step
-    // H = V + I, centred by +p/2 (V = 0 at t = 0)
-    rc = fhe::lwe_add(P.n, L.d_I, t ? V : NULL, half_p, cts, L.d_H, st);
+  // 1. WeightSums of the active layers, from the spikes of the previous
+  //    iteration (read before this iteration's bootstrap overwrites them)
+  for (uint32_t l = lo; l <= hi; ++l) {
+    Layer &L = S->layers[l];
+    const uint32_t t = tau - l;
+    const bool static_first = (l == 0 && S->desc.static_input);
+    if (static_first && t > 0) continue;  // the conv of the pixels is time-invariant
+    const uint32_t *x = (l == 0)
+                            ? S->d_input + (S->desc.static_input ? 0 : (size_t)t * ni * S->n_in * W)
+                            : spk + off[l - 1] * W;
+    if (L.type == FHE_LAYER_FC)
+      rc = fhe_lwe_linear(P.n, P.log2_p, L.d_w, L.out_size, L.in_size, NULL, x, ni, L.d_I, st);
+    else
+      rc = fhe_lwe_conv2d(P.n, P.log2_p, L.d_w, L.cin, L.h, L.w, L.cout, L.kh, L.kw, L.stride,
+                          L.pad, NULL, x, ni, L.d_I, st);
     if (rc) return rc;
-    if (S->profile) {
-      const size_t e = (size_t)t * S->layers.size() + li;
-      S->K->prof_ev0 = S->ev[2 * e];
-      S->K->prof_ev1 = S->ev[2 * e + 1];
-    }
-    rc = fhe_pbs_batch(S->K, L.d_H, cts, S->lut, L.d_out, S->desc.variant, st);
-    if (S->profile) {
-      S->ev_count[(size_t)t * S->layers.size() + li] = S->K->prof_count;
-      S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
-    }
-    if (rc) return rc;
-    x = L.d_out;  // spikes
   }
-  const Layer &last = S->layers.back();
-  const size_t cts = ni * last.out_size;
-  return fhe::lwe_add(P.n, last.d_out, t ? S->d_scores : NULL, 0u, cts, S->d_scores, st);
+  // 2. H = V + I, centred by +p/2 (V = 0 at the layer's first step)
+  for (uint32_t l = lo; l <= hi; ++l) {
+    const uint32_t t = tau - l;
+    rc = fhe::lwe_add(P.n, S->layers[l].d_I, t ? mem + off[l] * W : NULL, half_p,
+                      ni * S->layers[l].out_size, S->d_H + off[l] * W, st);
+    if (rc) return rc;
+  }
+  // 3. one bootstrap launch for every active neuron: spikes and V in place
+  if (S->profile) {
+    S->K->prof_ev0 = S->ev[2u * tau];
+    S->K->prof_ev1 = S->ev[2u * tau + 1u];
+  }
+  rc = fhe::pbs_run(S->K, S->d_H + off[lo] * W, off[hi + 1] - off[lo], S->lut, spk + off[lo] * W,
+                    all * W, S->desc.variant, st);
+  if (S->profile) {
+    S->ev_count[tau] = S->K->prof_count;
+    S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
+  }
+  if (rc) return rc;
+  // 4. spike-count scores of the last layer
+  if (hi == nl - 1u) {
+    const uint32_t t = tau - (nl - 1u);
+    rc = fhe::lwe_add(P.n, spk + off[nl - 1u] * W, t ? S->d_scores : NULL, 0u, ni * S->n_out,
+                      S->d_scores, st);
+    if (rc) return rc;
+  }
+  return FHE_OK;
 }
 
 static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
   for (auto &g : S->graphs)
     if (g) cudaGraphExecDestroy(g);
-  S->graphs.assign(S->desc.T, (cudaGraphExec_t)0);
-  S->graph_kernels.assign(S->desc.T, 0);
-  for (uint32_t t = 0; t < S->desc.T; ++t) {
+  const uint32_t iters = snn_iterations(S);
+  S->graphs.assign(iters, (cudaGraphExec_t)0);
+  S->graph_kernels.assign(iters, 0);
+  S->graph_images = 0;
+  for (uint32_t tau = 0; tau < iters; ++tau) {
     cudaGraph_t graph;
     FHE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     // launches enqueued while capturing run only when the graph is replayed
     const int64_t before = (int64_t)fhe::launches();
-    int rc = snn_step(S, t, ni, st);
-    S->graph_kernels[t] = (int64_t)fhe::launches() - before;
-    fhe::note_launches(-S->graph_kernels[t]);
+    int rc = snn_iteration(S, tau, ni, st);
+    S->graph_kernels[tau] = (int64_t)fhe::launches() - before;
+    fhe::note_launches(-S->graph_kernels[tau]);
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (rc) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
     FHE_CUDA_TRY(e);
-    cudaError_t ie = cudaGraphInstantiate(&S->graphs[t], graph, 0);
+    cudaError_t ie = cudaGraphInstantiate(&S->graphs[tau], graph, 0);
     cudaGraphDestroy(graph);
     FHE_CUDA_TRY(ie);
   }
@@ -254,38 +295,55 @@ static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
   return FHE_OK;
 }
 
-extern "C" int fhe_snn_infer(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
-                             int inputs_on_host, void *stream) {
-  if (!S || !ct_input || !scores || ni == 0 || ni > S->desc.max_images) return FHE_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  const fhe::Params &P = S->K->P;
-  const uint32_t W = P.n + 1u;
+extern "C" int fhe_snn_begin(fhe_snn *S, const uint32_t *ct_input, size_t ni, int inputs_on_host,
+                             void *stream) {
+  if (!S || !ct_input || ni == 0 || ni > S->desc.max_images) return FHE_EINVAL;
+  const uint32_t W = S->K->P.n + 1u;
   const size_t in_words = ni * (S->desc.static_input ? 1u : S->desc.T) * S->n_in * W;
   FHE_CUDA_TRY(cudaMemcpyAsync(S->d_input, ct_input, sizeof(uint32_t) * in_words,
-                               inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+                               inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+  S->cur_images = ni;
+  S->next_iter = 0;
+  return FHE_OK;
+}
+
+extern "C" int fhe_snn_step(fhe_snn *S, void *stream) {
+  if (!S || !S->cur_images) return FHE_EINVAL;
+  const uint32_t iters = snn_iterations(S);
+  if (S->next_iter >= iters) return FHE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ni = S->cur_images;
+  const uint32_t tau = S->next_iter;
   if (S->desc.use_graph & 1) {
-    FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
-    FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
-    if (S->graph_images != ni || S->graphs.size() != S->desc.T) {
+    if (S->graph_images != ni || S->graphs.size() != iters) {
+      FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
+      FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
       int rc = snn_capture(S, ni, S->gs);
       if (rc) return rc;
     }
-    for (uint32_t t = 0; t < S->desc.T; ++t) {
-      FHE_CUDA_TRY(cudaGraphLaunch(S->graphs[t], S->gs));
-      fhe::note_launches(S->graph_kernels[t]);
-    }
+    FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
+    FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
+    FHE_CUDA_TRY(cudaGraphLaunch(S->graphs[tau], S->gs));
+    fhe::note_launches(S->graph_kernels[tau]);
     FHE_CUDA_TRY(cudaEventRecord(S->join_out, S->gs));
     FHE_CUDA_TRY(cudaStreamWaitEvent(st, S->join_out, 0));
   } else {
-    for (uint32_t t = 0; t < S->desc.T; ++t) {
-      int rc = snn_step(S, t, ni, st);
-      if (rc) return rc;
-    }
+    int rc = snn_iteration(S, tau, ni, st);
+    if (rc) return rc;
   }
-  const size_t out_words = ni * S->n_out * W;
+  S->next_iter = tau + 1u;
+  return (int)(iters - S->next_iter);
+}
+
+extern "C" int fhe_snn_end(fhe_snn *S, uint32_t *scores, int inputs_on_host, void *stream) {
+  if (!S || !scores || !S->cur_images || S->next_iter != snn_iterations(S)) return FHE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t out_words = S->cur_images * S->n_out * (S->K->P.n + 1u);
   FHE_CUDA_TRY(cudaMemcpyAsync(scores, S->d_scores, sizeof(uint32_t) * out_words,
                                inputs_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-  S->last_images = ni;
+  S->last_images = S->cur_images;
+  S->cur_images = 0;
   if (inputs_on_host) {
     FHE_CUDA_TRY(cudaStreamSynchronize(st));
     return fhe_status(S->K, stream);
@@ -293,12 +351,26 @@ extern "C" int fhe_snn_infer(fhe_snn *S, const uint32_t *ct_input, size_t ni, ui
   return FHE_OK;
 }
 
+extern "C" int fhe_snn_infer(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
+                             int inputs_on_host, void *stream) {
+  if (!S || !scores) return FHE_EINVAL;
+  int rc = fhe_snn_begin(S, ct_input, ni, inputs_on_host, stream);
+  if (rc) return rc;
+  do {
+    rc = fhe_snn_step(S, stream);
+  } while (rc > 0);
+  if (rc < 0) { S->cur_images = 0; return rc; }
+  return fhe_snn_end(S, scores, inputs_on_host, stream);
+}
+
 extern "C" int fhe_snn_layer_spikes(const fhe_snn *S, uint32_t layer, uint32_t *dst,
                                     void *stream) {
   if (!S || !dst || layer >= S->layers.size() || !S->last_images) return FHE_EINVAL;
-  const Layer &L = S->layers[layer];
-  const size_t words = S->last_images * L.out_size * (S->K->P.n + 1u);
-  FHE_CUDA_TRY(cudaMemcpyAsync(dst, L.d_out, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice,
-                               (cudaStream_t)stream));
+  size_t off = 0;
+  for (uint32_t l = 0; l < layer; ++l) off += S->last_images * S->layers[l].out_size;
+  const uint32_t W = S->K->P.n + 1u;
+  const size_t words = S->last_images * S->layers[layer].out_size * W;
+  FHE_CUDA_TRY(cudaMemcpyAsync(dst, S->d_out + off * W, sizeof(uint32_t) * words,
+                               cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return FHE_OK;
 }

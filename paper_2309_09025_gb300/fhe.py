@@ -33,7 +33,8 @@ EXPORTED = (
     "fhe_lwe_conv2d", "fhe_lut_create", "fhe_lut_free", "fhe_pbs_batch", "fhe_status",
     "fhe_snn_create", "fhe_snn_free", "fhe_snn_pbs_per_image", "fhe_snn_infer",
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
-    "fhe_pbs_batch_noalloc",
+    "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
+    "fhe_snn_iterations",
 )
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
@@ -113,6 +114,10 @@ def lib():
                                                ctypes.POINTER(u64), ctypes.POINTER(u64)]),
             "fhe_kernel_launches": (u64, []),
             "fhe_pbs_batch_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp, vp]),
+            "fhe_snn_begin": (ctypes.c_int, [vp, vp, sz, ctypes.c_int, vp]),
+            "fhe_snn_step": (ctypes.c_int, [vp, vp]),
+            "fhe_snn_end": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+            "fhe_snn_iterations": (u32, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -348,6 +353,25 @@ class Snn:
             pin, pout = _ptr(ct_input), _ptr(scores)
         _check(lib().fhe_snn_infer(self.handle, pin, n_images, pout, int(bool(on_host)),
                                    _stream(stream)), "snn_infer")
+        return scores
+
+    def iterations(self):
+        return int(lib().fhe_snn_iterations(self.handle))
+
+    def begin(self, ct_input, n_images, stream=None):
+        """Stage a device input and reset the state (fhe_snn_begin)."""
+        _check(lib().fhe_snn_begin(self.handle, _ptr(ct_input), n_images, 0, _stream(stream)),
+               "snn_begin")
+
+    def step(self, stream=None):
+        """One layer-skewed step; returns the number of steps still to run."""
+        rc = lib().fhe_snn_step(self.handle, _stream(stream))
+        if rc < 0:
+            _check(rc, "snn_step")
+        return rc
+
+    def end(self, scores, stream=None):
+        _check(lib().fhe_snn_end(self.handle, _ptr(scores), 0, _stream(stream)), "snn_end")
         return scores
 
     def profile(self):
