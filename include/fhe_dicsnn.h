@@ -187,6 +187,14 @@ int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe
 int fhe_pbs_batch_noalloc(const fhe_keys *keys, const uint32_t *ct_in, size_t count,
                           const fhe_lut *lut, uint32_t *ct_out, void *stream);
 
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * thread that waits, with the bounded-wait pattern of the bootstrap kernels,
+ * on an mbarrier that nothing completes; after `limit_us` microseconds
+ * (1 .. 1e6) it gives up and records FHE_ETIMEOUT in the status word.  Then
+ * returns fhe_status(keys, stream), i.e. FHE_ETIMEOUT when the path works.
+ * No fault, trap or endless wait is involved. */
+int fhe_selftest_timeout(fhe_keys *keys, uint32_t limit_us, void *stream);
+
 /* Device status word: FHE_OK, or FHE_ETIMEOUT if a bounded device wait gave
  * up since the last call.  Synchronizes `stream`, then clears the word. */
 int fhe_status(fhe_keys *keys, void *stream);

@@ -73,6 +73,24 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// completes, with the same bounded-wait pattern as the bootstrap kernels but a
+// caller-chosen limit; when it gives up it records FHE_ETIMEOUT in the status
+// word, which the host reads with fhe_status.  Nothing faults or hangs.
+__global__ void k_selftest_timeout(uint64_t limit_ns, int *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(&bar, 0u)) {
+    if (global_ns() - t0 > limit_ns) {
+      atomicExch(status, FHE_ETIMEOUT);
+      return;
+    }
+  }
+}
+
 struct LutArgs {
   uint32_t L;
   const uint32_t *tv;
@@ -467,6 +485,15 @@ int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut
 }
 
 }  // namespace fhe
+
+extern "C" int fhe_selftest_timeout(fhe_keys *K, uint32_t limit_us, void *stream) {
+  if (!K || limit_us == 0 || limit_us > 1000000u) return FHE_EINVAL;
+  k_selftest_timeout<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_us * 1000ull,
+                                                         K->d_status);
+  fhe::note_launches(1);
+  FHE_CUDA_TRY(cudaGetLastError());
+  return fhe_status(K, stream);
+}
 
 extern "C" int fhe_pbs_batch(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                              uint32_t *ct_out, int variant, void *stream) {

@@ -34,7 +34,7 @@ EXPORTED = (
     "fhe_snn_create", "fhe_snn_free", "fhe_snn_pbs_per_image", "fhe_snn_infer",
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
-    "fhe_snn_iterations",
+    "fhe_snn_iterations", "fhe_selftest_timeout",
 )
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
@@ -118,6 +118,7 @@ def lib():
             "fhe_snn_step": (ctypes.c_int, [vp, vp]),
             "fhe_snn_end": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
             "fhe_snn_iterations": (u32, [vp]),
+            "fhe_selftest_timeout": (ctypes.c_int, [vp, u32, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -191,6 +192,10 @@ class Keys:
         _check(lib().fhe_keys_export(self.handle, which, out.ctypes.data_as(ctypes.c_void_p),
                                      size), "keys_export")
         return out
+
+    def selftest_timeout(self, limit_us=20000, stream=None):
+        """Bounded-wait self-test; returns FHE_ETIMEOUT when detection works."""
+        return lib().fhe_selftest_timeout(self.handle, int(limit_us), _stream(stream))
 
     def status(self, stream=None):
         return lib().fhe_status(self.handle, _stream(stream))

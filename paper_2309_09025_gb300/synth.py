@@ -125,6 +125,32 @@ def csnn_net(seed=2, T=4, divisors=CSNN_DIVISORS, raw=False):
             "n_in": 28 * 28}
 
 
+def paper_csnn_net(seed=6, T=2, wmax=3):
+    """The paper's CSNN (3.1): conv 1->10, 8x8, stride 2, padding 1 (10x12x12
+    LIF) -> 2x2 average pooling -> FC 360->160 LIF -> FC 160->10 LIF.
+
+    The pooling layer is a WeightSum too; its division is moved into the next
+    layer's weights (3.3, multi-level discretization: Discret(w, theta/n)), so
+    pooling + FC compose into one integer FC 1440->160 whose weight for input
+    (c, y, x) is the FC weight of the pooled cell (c, y//2, x//2).  Weights are
+    seeded integers in [-wmax, wmax] (the trained weights are not available).
+    """
+    g = rng(seed)
+    Wc = g.integers(-wmax, wmax + 1, size=(10, 1, 8, 8), dtype=np.int64)
+    Wfc = g.integers(-wmax, wmax + 1, size=(160, 10, 6, 6), dtype=np.int64)
+    W2 = g.integers(-wmax, wmax + 1, size=(10, 160), dtype=np.int64)
+    # compose the 2x2 sum pooling (division folded into Wfc) with FC 360->160
+    W1 = np.repeat(np.repeat(Wfc, 2, axis=2), 2, axis=3).reshape(160, 10 * 12 * 12)
+    layers = [
+        {"type": "conv", "W": Wc.astype(np.int32), "cin": 1, "h": 28, "w": 28, "stride": 2,
+         "pad": 1},
+        {"type": "fc", "W": W1.astype(np.int32)},
+        {"type": "fc", "W": W2.astype(np.int32)},
+    ]
+    return {"layers": layers, "lif": dict(LIF_DEFAULT), "T": T, "static_input": True,
+            "n_in": 28 * 28}
+
+
 def ragged_batch_sizes(seed, total, lo=1, hi=64):
     """Arrival batch sizes uniform in [lo, hi] that sum to `total`."""
     g = rng(seed)

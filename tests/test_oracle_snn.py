@@ -108,3 +108,22 @@ def test_encrypted_conv_snn_static_input(oracle_keys):
     got = O.decrypt(P, K, enc["spikes"][0].reshape(-1, P["n"] + 1)).reshape(2, -1)
     assert np.array_equal(got, plain["spikes"][0])
     assert np.array_equal(O.decrypt(P, K, enc["scores"]), plain["scores"])
+
+
+def test_paper_csnn_pool_folded_into_fc():
+    """3.3: the 2x2 average pooling's division moved into the next layer's
+    weights -- the composed FC equals sum-pooling followed by the FC, checked
+    on random spike maps by brute force."""
+    net = synth.paper_csnn_net(seed=6)
+    W1 = net["layers"][1]["W"].astype(np.int64)
+    g = np.random.default_rng(0)
+    Wfc = synth.rng(6)
+    Wc = Wfc.integers(-3, 4, size=(10, 1, 8, 8), dtype=np.int64)  # same draw order
+    Wp = Wfc.integers(-3, 4, size=(160, 10, 6, 6), dtype=np.int64)
+    for _ in range(5):
+        s = g.integers(0, 2, (10, 12, 12))
+        pooled = s.reshape(10, 6, 2, 6, 2).sum(axis=(2, 4))
+        ref = np.tensordot(Wp, pooled, axes=([1, 2, 3], [0, 1, 2]))
+        assert np.array_equal(W1 @ s.reshape(-1), ref)
+    assert np.array_equal(net["layers"][0]["W"], Wc)
+    assert net["layers"][0]["pad"] == 1 and W1.shape == (160, 1440)
