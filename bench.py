@@ -106,6 +106,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, device):
+    """Slowest rank's time (the job ends when the last replica ends)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(pbs_per_rank, world, max_ms):
+    """Whole-job bootstraps per second: every replica's work over the
+    slowest replica's time (weak scaling, no exchange between replicas)."""
+    return pbs_per_rank * world / (max_ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,14 +253,8 @@ def run_ours(args):
     barrier()
     launches = fhe.kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    total_pbs = per_image * B * args.steps * world
-    value = total_pbs / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    value = job_rate(per_image * B * args.steps, world, total_ms)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -261,13 +272,8 @@ def run_ours(args):
             snn.infer(h_in, B, h_out, on_host=True)
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
-        e2e_total = sum(e2e_ms)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
-        e2e = {"value": per_image * B * args.e2e_steps * world / (e2e_total / 1e3), "unit": UNIT,
+        e2e_total = max_over_ranks(sum(e2e_ms), world, "cuda")
+        e2e = {"value": job_rate(per_image * B * args.e2e_steps, world, e2e_total), "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel() * 4),
                "d2h_bytes_per_step": int(h_out.numel() * 4)}
 

@@ -47,7 +47,9 @@ constexpr int kCluster = 4;
 constexpr int kBt = 128;          // ciphertexts per cluster (MMA M)
 constexpr int kBN = 256;          // output coefficients per block (MMA N)
 constexpr int kKB = 64;           // K elements per A tile
-constexpr int kAStages = 10;
+// A-operand pipeline depth: 10 stages at N = 1024, 8 at N = 2048 (the B
+// windows grow with N; both fit in 227 KB of shared memory).
+__host__ __device__ constexpr uint32_t tc_stages(uint32_t N) { return N <= 1024u ? 10u : 8u; }
 constexpr int kATile = kBt * kKB * 2;   // 16 KB
 constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
 constexpr int kTmemCols = 512;
@@ -224,7 +226,7 @@ struct TcSmem {
 __host__ __device__ inline TcSmem tc_smem(uint32_t N) {
   TcSmem s;
   uint32_t o = 0;
-  s.a = o; o += kAStages * kATile;
+  s.a = o; o += tc_stages(N) * kATile;
   s.b = o; o += 2u * ((kBN + N) / 8u) * 128u;
   s.bars = o; o += 32u * 8u;
   s.tmem_slot = o; o += 16u;
@@ -244,8 +246,10 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
     k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
                       const uint32_t *__restrict__ ct_in, size_t count, TcLut lut,
                       uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
-                      uint32_t chunk_r, uint32_t *__restrict__ big_out, int *status) {
+                      uint32_t chunk_r, uint32_t sub_shift, uint32_t *__restrict__ big_out,
+                      int *status) {
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
+  constexpr uint32_t kAStages = tc_stages(N);
   constexpr uint32_t WIN = (kBN + N) / 8u;   // core matrices in one B window
   constexpr uint32_t KBLK = N / kKB;         // A tiles per key row r
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -258,6 +262,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t *t_full = b_empty + 2, *t_empty = t_full + 2;
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
+  __shared__ uint32_t s_abar[32];  // a~_i of this CTA's 32 ciphertexts
 
   const uint32_t n = P.n, l = P.l, R = 2u * l;
   const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
@@ -265,11 +270,16 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   const uint64_t tile = blockIdx.x / kCluster;
   const size_t base = (size_t)tile * kBt;
   uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);            // [128][2][N]
-  __half *dig = dig_g + tile * tc_tile_dig_halves(N, R);
+  __half *dig = dig_g + tile * tc_tile_dig_halves(N, sub_shift ? 4u * l : 2u * l);
   const uint32_t jq = q / 2u;                 // output polynomial of this CTA
   const uint32_t cq = (q % 2u) * (N / 2u);    // first output coefficient
   const uint32_t nblk = (N / 2u) / kBN;       // blocks of 256 per CTA
-  const uint32_t nchunk = R / chunk_r;
+  // With sub_shift > 0 every gadget digit d is split into two signed
+  // sub-digits d = hi * 2^sub_shift + lo (rows r and R + r of the digit
+  // operand) so that each fp32 partial sum stays within 2^24; chunks never mix
+  // low and high rows, and high rows are scaled by 2^sub_shift when drained.
+  const uint32_t RR = sub_shift ? 2u * R : R;
+  const uint32_t nchunk = RR / chunk_r;
   const uint64_t strip_halves = (uint64_t)(N / 4u) * 64u;
 
   if (tid == 0) {
@@ -314,50 +324,58 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 
   for (uint32_t i = 0; i < n; ++i) {
     // ---- digits of X^{a~_i} ACC - ACC for this CTA's 32 ciphertexts.
-    // A group = 8 consecutive coefficients c0..c0+7 of one polynomial: their
-    // reversed indices t' = N-1-c form exactly one 8-element core-matrix row,
-    // so each gadget level is one 16-byte store.
-    for (uint32_t grp = tid; grp < 32u * 2u * (N / 8u); grp += kThreads) {
-      const uint32_t c0 = (grp % (N / 8u)) * 8u;
-      const uint32_t j = (grp / (N / 8u)) & 1u;
-      const uint32_t b = 32u * q + grp / (2u * (N / 8u));
+    // One warp per chunk of 256 coefficients of one polynomial; lane L owns
+    // coefficients c = c_base + 32k + L (k < 8), so every load and store
+    // instruction of the warp is coalesced (the reversed index t' = N-1-c of
+    // 32 consecutive c spans four 16-byte core-matrix rows).
+    if (tid < 32u) {
+      const uint32_t b = 32u * q + tid;
       const uint32_t av = (base + b < count) ? __ldg(ct_in + (base + b) * (n + 1u) + i) : 0u;
-      const uint32_t a = fhe::mod_switch_2n(av, LOG2_2N);
+      s_abar[tid] = fhe::mod_switch_2n(av, LOG2_2N);
+    }
+    __syncthreads();
+    constexpr uint32_t CHUNKS = 32u * 2u * (N / 256u);
+    for (uint32_t chunk = warp; chunk < CHUNKS; chunk += kThreads / 32u) {
+      const uint32_t cb = chunk % (N / 256u), j = (chunk / (N / 256u)) & 1u;
+      const uint32_t bl = chunk / (2u * (N / 256u));  // row within this CTA's 32
+      const uint32_t b = 32u * q + bl;
+      const uint32_t a = s_abar[bl];
       const uint32_t *Pj = acc + ((uint64_t)b * 2u + j) * N;
-      uint32_t own[8], rot[8];
-      const uint4 o0 = *reinterpret_cast<const uint4 *>(Pj + c0);
-      const uint4 o1 = *reinterpret_cast<const uint4 *>(Pj + c0 + 4u);
-      own[0] = o0.x; own[1] = o0.y; own[2] = o0.z; own[3] = o0.w;
-      own[4] = o1.x; own[5] = o1.y; own[6] = o1.z; own[7] = o1.w;
-#pragma unroll
-      for (uint32_t k = 0; k < 8u; ++k) {
-        const uint32_t s = (c0 + k + 2u * N - a) & (2u * N - 1u);
-        rot[k] = (s < N) ? Pj[s] : (0u - Pj[s - N]);
-      }
       uint32_t xr[8];
 #pragma unroll
       for (uint32_t k = 0; k < 8u; ++k) {
-        const uint32_t x = rot[k] - own[k];
-        xr[k] = (total_bits >= 32u)
-                    ? x
-                    : ((uint32_t)(x + (1u << (31u - total_bits))) >> (32u - total_bits));
+        const uint32_t c = cb * 256u + 32u * k + lane;
+        const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
+        const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
+        xr[k] = rot - Pj[c];
       }
-      const uint32_t tp0 = N - 8u - c0;  // smallest t' of the group
-      const uint32_t in_tile = (b / 8u) * 512u + ((tp0 % 64u) / 8u) * 64u + (b % 8u) * 8u;
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k)
+        xr[k] = (total_bits >= 32u)
+                    ? xr[k]
+                    : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
       // least significant level first (carries propagate upwards)
       for (int lam = (int)l - 1; lam >= 0; --lam) {
-        __align__(16) __half row[8];  // t' = N-1-(c0+k) sits at position 7-k
+        const uint32_t r = j * l + (uint32_t)lam;
 #pragma unroll
         for (uint32_t k = 0; k < 8u; ++k) {
           const uint32_t d = xr[k] & Bmask;
           xr[k] >>= P.log2_bg;
           int32_t sd = (int32_t)d;
           if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
-          row[7u - k] = __int2half_rn(sd);
+          const uint32_t tp = N - 1u - (cb * 256u + 32u * k + lane);  // reversed index t'
+          const uint32_t in_tile = (b / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (b % 8u) * 8u + (tp % 8u);
+          if (sub_shift == 0u) {
+            dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(sd);
+          } else {
+            const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
+            int32_t lo = (int32_t)((uint32_t)sd & sm);
+            if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
+            const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
+            dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(lo);
+            dig[(uint64_t)((R + r) * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(hi);
+          }
         }
-        const uint32_t r = j * l + (uint32_t)lam;
-        *reinterpret_cast<uint4 *>(dig + (uint64_t)(r * KBLK + tp0 / 64u) * (kATile / 2) + in_tile) =
-            *reinterpret_cast<const uint4 *>(row);
       }
     }
     // The digits this CTA multicasts are the ones it just wrote (rows 32q..);
@@ -377,7 +395,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                 const uint32_t bs = b_it & 1u;
                 if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
                 if (!s_abort) {
-                  const __half *src = strips + ((((uint64_t)i * R + r) * 2u + jq) * 4u + L) * strip_halves +
+                  const __half *src = strips + ((((uint64_t)i * R + r % R) * 2u + jq) * 4u + L) * strip_halves +
                                       (uint64_t)(c0 / 8u) * 64u;
                   mbar_expect_tx(&b_full[bs], WIN * 128u);
                   bulk_g2s(sB + bs * WIN * 128u, src, WIN * 128u, &b_full[bs]);
@@ -450,6 +468,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
         for (uint32_t L = 0; L < 4u; ++L)
           for (uint32_t ch = 0; ch < nchunk; ++ch) {
             const uint32_t buf = u_it & 1u;
+            const uint32_t shift = 8u * L + ((ch * chunk_r >= R) ? sub_shift : 0u);
             const bool got = wait_bounded(&t_full[buf], (u_it >> 1) & 1u, &s_abort);
             const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
             tc_fence_after();
@@ -462,7 +481,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
                   const int32_t v = __float2int_rn(__uint_as_float(r[k]));
-                  outv[part * 32 + k] += (uint32_t)v << (8u * L);
+                  outv[part * 32 + k] += (uint32_t)v << shift;
                 }
               }
             }
@@ -475,10 +494,16 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
           const uint32_t c0 = cq + blk * kBN + half * 128u;
           uint32_t *dst = acc + ((uint64_t)b * 2u + jq) * N + c0;
 #pragma unroll
-          for (int k = 0; k < 128; k += 4) {
-            uint4 v = *reinterpret_cast<uint4 *>(dst + k);
-            v.x += outv[k]; v.y += outv[k + 1]; v.z += outv[k + 2]; v.w += outv[k + 3];
-            *reinterpret_cast<uint4 *>(dst + k) = v;
+          for (int k0 = 0; k0 < 128; k0 += 16) {  // 4 loads in flight, then the stores
+            uint4 v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = *reinterpret_cast<const uint4 *>(dst + k0 + 4 * m);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int k = k0 + 4 * m;
+              v[m].x += outv[k]; v[m].y += outv[k + 1]; v[m].z += outv[k + 2]; v[m].w += outv[k + 3];
+              *reinterpret_cast<uint4 *>(dst + k) = v[m];
+            }
           }
         }
       }
@@ -535,10 +560,21 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 
 namespace fhe {
 
-// Largest number of key rows r per fp32 accumulation that keeps every partial
-// sum within 2^24: (Bg/2) * 128 * chunk_r * N <= 2^24.
-static uint32_t tc_chunk_r(const Params &P) {
+// Sub-digit split shift: 0 when the gadget digits (|d| <= Bg/2) keep one key
+// row's fp32 partial sums within 2^24, else ceil(log2_bg / 2) (each digit then
+// becomes two signed sub-digits of magnitude <= 2^(shift-1)).
+static uint32_t tc_sub_shift(const Params &P) {
   const uint64_t per_r = (uint64_t)(1u << (P.log2_bg - 1u)) * 128u * P.N;
+  return per_r <= (1ull << 24) ? 0u : (P.log2_bg + 1u) / 2u;
+}
+
+// Largest number of digit rows per fp32 accumulation that keeps every partial
+// sum within 2^24: max|digit| * 128 * chunk_r * N <= 2^24; the chunk divides
+// the key rows so that low and high sub-digit rows never share a chunk.
+static uint32_t tc_chunk_r(const Params &P) {
+  const uint32_t s = tc_sub_shift(P);
+  const uint64_t dmax = s ? (1ull << (s - 1u)) : (1ull << (P.log2_bg - 1u));
+  const uint64_t per_r = dmax * 128u * P.N;
   uint32_t cr = 0;
   while ((uint64_t)(cr + 1u) * per_r <= (1ull << 24) && cr + 1u <= P.rows()) ++cr;
   while (cr > 0 && P.rows() % cr) --cr;
@@ -546,8 +582,13 @@ static uint32_t tc_chunk_r(const Params &P) {
 }
 
 static bool tc_supported(const Params &P) {
-  return P.k == 1u && P.N == 1024u && tc_chunk_r(P) >= 1u;
+  const uint32_t s = tc_sub_shift(P);
+  // the high sub-digit must also fit: |hi| <= 2^(log2_bg - s - 1) + 1 <= 2^(s-1)
+  if (s && (1u << (P.log2_bg - s - 1u)) > (1u << (s - 1u))) return false;
+  return P.k == 1u && (P.N == 1024u || P.N == 2048u) && tc_chunk_r(P) >= 1u;
 }
+
+static uint32_t tc_digit_rows(const Params &P) { return tc_sub_shift(P) ? 2u * P.rows() : P.rows(); }
 
 int tc_prepare(fhe_keys *K) {
   const Params &P = K->P;
@@ -558,7 +599,7 @@ int tc_prepare(fhe_keys *K) {
   if (cudaMalloc(&K->d_bsk_tc, K->bsk_tc_bytes) != cudaSuccess) return FHE_ENOMEM;
   if (cudaMalloc(&K->d_acc_tc, sizeof(uint32_t) * tiles * tc_tile_acc_words(P.N)) != cudaSuccess)
     return FHE_ENOMEM;
-  if (cudaMalloc(&K->d_digits_tc, sizeof(__half) * tiles * tc_tile_dig_halves(P.N, P.rows())) !=
+  if (cudaMalloc(&K->d_digits_tc, sizeof(__half) * tiles * tc_tile_dig_halves(P.N, tc_digit_rows(P))) !=
       cudaSuccess)
     return FHE_ENOMEM;
   k_hankel_strips<<<152u * 16u, 256>>>(P, K->d_bsk, (__half *)K->d_bsk_tc);
@@ -587,9 +628,9 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   la.rval = lut->d_rval;
   la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
   la.off0 = lut->off[0]; la.off1 = lut->off[1];
-  const uint32_t chunk_r = tc_chunk_r(P);
+  const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem(P.N);
-  auto kern = k_blind_rotate_tc<1024>;
+  auto kern = (P.N == 1024u) ? k_blind_rotate_tc<1024> : k_blind_rotate_tc<2048>;
   FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
@@ -598,7 +639,7 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
     if (prof) { FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev0, st, cudaEventRecordExternal)); K->prof_count = cnt; }
     kern<<<tiles * kCluster, kThreads, S.total, st>>>(
         P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
-        (__half *)K->d_digits_tc, chunk_r, K->d_big, K->d_status);
+        (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status);
     note_launches(1);
     FHE_CUDA_TRY(cudaGetLastError());
     if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));

@@ -1,0 +1,50 @@
+"""Multi-rank bench logic on CPU: two gloo ranks (replicas of the encrypted
+inference, no data-path exchange) agree on the slowest rank's time and on
+the whole-job rate."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    import bench
+    w, r, local = bench.dist_setup()
+    assert (w, r, local) == (world, rank, rank)
+    ms = 1000.0 * (rank + 1)  # rank 1 is the slowest replica
+    slowest = bench.max_over_ranks(ms, world, "cpu")
+    rate = bench.job_rate(5160 * 7, world, slowest)
+    out[rank] = (slowest, rate)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_max_time_and_job_rate():
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, join=True,
+                       start_method="spawn")
+    assert out[0] == out[1]
+    slowest, rate = out[0]
+    assert slowest == 2000.0
+    assert rate == pytest.approx(5160 * 7 * 2 / 2.0)
