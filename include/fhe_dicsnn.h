@@ -49,6 +49,10 @@ extern "C" {
 #define FHE_VARIANT_TC 1    /* exact external product on tcgen05 tensor cores,
                                key split into 8-bit limbs (fp16 operands, fp32
                                accumulation kept below 2^24)                 */
+#define FHE_VARIANT_FFT 2   /* conventional FP64 negacyclic FFT product (the
+                               paper's "FFT technology", 5.3): NOT bit-exact,
+                               outputs rounded from doubles; see
+                               fhe_fft_max_error                              */
 
 /* Which key to export (fhe_keys_export / fhe_keys_size). */
 #define FHE_KEY_LWE 0  /* s:   uint32_t[n], entries 0/1                        */
@@ -186,6 +190,12 @@ int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe
 #define FHE_PBS_NOALLOC_MAX_WORDS (1u << 20)
 int fhe_pbs_batch_noalloc(const fhe_keys *keys, const uint32_t *ct_in, size_t count,
                           const fhe_lut *lut, uint32_t *ct_out, void *stream);
+
+/* Largest distance to the nearest integer of any external-product output of
+ * the FFT variant since the last reset (units of 2^-32 torus, i.e. of one
+ * uint32 step): below 0.5 every output was rounded to the exact value.
+ * Synchronizes; reset != 0 clears it.  0.0 before the first FFT call. */
+int fhe_fft_max_error(fhe_keys *keys, double *max_err, int reset);
 
 /* Failure-detection self-test (no counterpart in the paper): launches one
  * thread that waits, with the bounded-wait pattern of the bootstrap kernels,

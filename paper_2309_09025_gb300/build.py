@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfhe_dicsnn.so")
 SOURCES = ["fhe_keys.cu", "fhe_linear.cu", "fhe_pbs_exact.cu", "fhe_pbs_tc.cu", "fhe_snn.cu",
-           "fhe_noalloc.cu"]
+           "fhe_noalloc.cu", "fhe_pbs_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

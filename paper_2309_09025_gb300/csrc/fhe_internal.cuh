@@ -120,6 +120,10 @@ struct fhe_keys {
   // this event pair and its ciphertext count stored in prof_count
   cudaEvent_t prof_ev0, prof_ev1;
   size_t prof_count;
+  // FP64 FFT variant (built on first use): twist table, FFT twiddles, key
+  // spectra, largest rounding distance seen (bits of a double)
+  void *d_fft_twist, *d_fft_tw, *d_fft_kspec;
+  unsigned long long *d_fft_maxerr;
 };
 
 struct fhe_lut {
@@ -153,6 +157,9 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
               uint32_t *ct_out, size_t table_stride, cudaStream_t st);
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
            uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+int pbs_fft(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+            uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+int fft_prepare(fhe_keys *K);
 // Dispatch on the variant (FHE_EINVAL for an unknown one).
 int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
             uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st);

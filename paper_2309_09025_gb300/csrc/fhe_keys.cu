@@ -164,6 +164,10 @@ static void keys_release(fhe_keys *K) {
   cudaFree(K->d_bsk_tc);
   cudaFree(K->d_acc_tc);
   cudaFree(K->d_digits_tc);
+  cudaFree(K->d_fft_twist);
+  cudaFree(K->d_fft_tw);
+  cudaFree(K->d_fft_kspec);
+  cudaFree(K->d_fft_maxerr);
   free(K);
 }
 

@@ -481,6 +481,7 @@ int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut
   if (!count) return FHE_OK;
   if (variant == FHE_VARIANT_EXACT) return pbs_exact(K, ct_in, count, lut, ct_out, table_stride, st);
   if (variant == FHE_VARIANT_TC) return pbs_tc(K, ct_in, count, lut, ct_out, table_stride, st);
+  if (variant == FHE_VARIANT_FFT) return pbs_fft(K, ct_in, count, lut, ct_out, table_stride, st);
   return FHE_EINVAL;
 }
 

@@ -610,6 +610,7 @@ int tc_prepare(fhe_keys *K) {
 }
 
 int pbs_prepare(fhe_keys *K, int variant) {
+  if (variant == FHE_VARIANT_FFT) return fft_prepare(K);
   if (variant != FHE_VARIANT_TC) return FHE_OK;
   if (!tc_supported(K->P)) return FHE_EUNSUPPORTED;
   return tc_prepare(K);

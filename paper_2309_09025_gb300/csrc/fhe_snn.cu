@@ -91,7 +91,9 @@ static void snn_release(fhe_snn *S) {
 extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out) {
   if (!K || !d || !out || !d->layers || d->n_layers == 0 || d->T == 0 || d->max_images == 0)
     return FHE_EINVAL;
-  if (d->variant != FHE_VARIANT_EXACT && d->variant != FHE_VARIANT_TC) return FHE_EINVAL;
+  if (d->variant != FHE_VARIANT_EXACT && d->variant != FHE_VARIANT_TC &&
+      d->variant != FHE_VARIANT_FFT)
+    return FHE_EINVAL;
   *out = NULL;
   const fhe::Params &P = K->P;
   const int32_t p = (int32_t)P.p();

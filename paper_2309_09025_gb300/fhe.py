@@ -22,6 +22,7 @@ FHE_ETIMEOUT = -4
 FHE_EUNSUPPORTED = -5
 VARIANT_EXACT = 0
 VARIANT_TC = 1
+VARIANT_FFT = 2
 KEY_LWE, KEY_GLWE, KEY_BSK, KEY_KSK = 0, 1, 2, 3
 LAYER_FC, LAYER_CONV = 0, 1
 SNN_PROFILE = 2
@@ -34,7 +35,7 @@ EXPORTED = (
     "fhe_snn_create", "fhe_snn_free", "fhe_snn_pbs_per_image", "fhe_snn_infer",
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
-    "fhe_snn_iterations", "fhe_selftest_timeout",
+    "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
 )
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
@@ -119,6 +120,7 @@ def lib():
             "fhe_snn_end": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
             "fhe_snn_iterations": (u32, [vp]),
             "fhe_selftest_timeout": (ctypes.c_int, [vp, u32, vp]),
+            "fhe_fft_max_error": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -192,6 +194,13 @@ class Keys:
         _check(lib().fhe_keys_export(self.handle, which, out.ctypes.data_as(ctypes.c_void_p),
                                      size), "keys_export")
         return out
+
+    def fft_max_error(self, reset=False):
+        """Largest rounding distance of the FFT variant's products so far."""
+        v = ctypes.c_double()
+        _check(lib().fhe_fft_max_error(self.handle, ctypes.byref(v), int(bool(reset))),
+               "fft_max_error")
+        return v.value
 
     def selftest_timeout(self, limit_us=20000, stream=None):
         """Bounded-wait self-test; returns FHE_ETIMEOUT when detection works."""

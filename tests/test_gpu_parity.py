@@ -101,7 +101,7 @@ def _luts(P, L):
     return O.lif_luts(P, v_th=8 if p >= 32 else 2, leak_shift=1, spike_scale=1)
 
 
-VARIANTS = ["EXACT", "TC"]
+VARIANTS = ["EXACT", "TC"]  # bit-exact variants
 
 
 def pbs(fhe, K, ct, lut, variant):
@@ -275,3 +275,42 @@ def test_snn_toy_layer_tc_bit_exact(fhe, oracle_keys):
     snn.infer(torch.from_numpy(ct.view(np.int32)).cuda(), 1, scores)
     ref = O.snn_encrypted(P, OK, net, ct[:, 0], nthreads=NTHREADS)
     assert np.array_equal(u32(scores)[0], ref["scores"])
+
+
+@pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 257)])
+def test_fft_variant_decrypts_like_exact(fhe, oracle_keys, name, count):
+    """FP64 FFT blind rotation (not bit-exact by design): every output decrypts
+    to the exact path's message; most outputs are even bit-identical (the
+    rounded doubles hit the exact integers); the rounding-error report is set."""
+    P, K = gpu_keys(fhe, name, 3)
+    _, OK = oracle_keys(name, 3)
+    p = 1 << P["log2_p"]
+    m = synth.uniform_messages(43, count, p)
+    ct = fhe.encrypt(K, m, seed=17)
+    for L in (1, 2):
+        luts = _luts(P, L)
+        lut = fhe.lut_create(K, luts)
+        ref = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
+        K.fft_max_error(reset=True)
+        got = u32(pbs(fhe, K, ct, lut, "FFT"))
+        err = K.fft_max_error()
+        assert 0.0 < err < 0.5
+        for j in range(L):
+            assert np.array_equal(O.decrypt(P, OK, got[j]), O.decrypt(P, OK, ref[j]))
+        assert np.mean(np.all(got == ref, axis=-1)) > 0.9
+
+
+def test_snn_toy_layer_fft_decrypts_like_plain(fhe, oracle_keys):
+    """Encrypted LIF layer on the FFT path: decrypted spike counts equal the
+    plaintext network (low-noise ring N=1024)."""
+    P, K = gpu_keys(fhe, "T0", 2)
+    _, OK = oracle_keys("T0", 2)
+    net = synth.toy_lif_net(seed=4)
+    net["lif"] = dict(v_th=3, leak_shift=1, spike_scale=1)
+    x = synth.bernoulli_spikes(5, 2, 16, 0.3)
+    ct = O.encrypt(P, OK, x.reshape(-1), 9).reshape(2, 1, 16, -1)
+    snn = fhe.Snn(K, net, max_images=1, variant=fhe.VARIANT_FFT, use_graph=True)
+    scores = torch.empty((1, 32, P["n"] + 1), dtype=torch.int32, device="cuda")
+    snn.infer(torch.from_numpy(ct.view(np.int32)).cuda(), 1, scores)
+    plain = O.snn_plain(P, net, x)
+    assert np.array_equal(O.decrypt(P, OK, u32(scores)[0]), plain["scores"])
