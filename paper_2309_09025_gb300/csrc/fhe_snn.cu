@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <vector>
 
 #include "fhe_internal.cuh"
@@ -48,9 +49,14 @@ struct fhe_snn {
   // inference in progress
   size_t cur_images;
   uint32_t next_iter;
-  size_t graph_images;
-  std::vector<cudaGraphExec_t> graphs;  // one per iteration
-  std::vector<int64_t> graph_kernels;   // kernel nodes of each graph
+  // captured graphs per batch size: one executable graph per iteration, its
+  // kernel-node count and its bracketed bootstrap count
+  struct GraphSet {
+    std::vector<cudaGraphExec_t> execs;
+    std::vector<int64_t> kernels;
+    std::vector<size_t> pbs_counts;
+  };
+  std::map<size_t, GraphSet> graphs;
   // Graphs are captured and replayed on a library-owned non-blocking stream
   // (the legacy default stream cannot be captured), joined to the caller's
   // stream by the two events below.
@@ -69,8 +75,9 @@ static uint32_t snn_iterations(const fhe_snn *S) {
 
 static void snn_release(fhe_snn *S) {
   if (!S) return;
-  for (auto &g : S->graphs)
-    if (g) cudaGraphExecDestroy(g);
+  for (auto &kv : S->graphs)
+    for (auto &g : kv.second.execs)
+      if (g) cudaGraphExecDestroy(g);
   for (auto &e : S->ev)
     if (e) cudaEventDestroy(e);
   if (S->join_in) cudaEventDestroy(S->join_in);
@@ -271,29 +278,41 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
   return FHE_OK;
 }
 
+// Capture the iterations for batch size ni (kept for later calls of the same
+// size; at most max_images sets exist).
 static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
-  for (auto &g : S->graphs)
-    if (g) cudaGraphExecDestroy(g);
   const uint32_t iters = snn_iterations(S);
-  S->graphs.assign(iters, (cudaGraphExec_t)0);
-  S->graph_kernels.assign(iters, 0);
-  S->graph_images = 0;
-  for (uint32_t tau = 0; tau < iters; ++tau) {
+  fhe_snn::GraphSet set;
+  set.execs.assign(iters, (cudaGraphExec_t)0);
+  set.kernels.assign(iters, 0);
+  set.pbs_counts.assign(iters, 0);
+  int rc = FHE_OK;
+  for (uint32_t tau = 0; tau < iters && rc == FHE_OK; ++tau) {
     cudaGraph_t graph;
-    FHE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = FHE_ECUDA;
+      break;
+    }
     // launches enqueued while capturing run only when the graph is replayed
     const int64_t before = (int64_t)fhe::launches();
-    int rc = snn_iteration(S, tau, ni, st);
-    S->graph_kernels[tau] = (int64_t)fhe::launches() - before;
-    fhe::note_launches(-S->graph_kernels[tau]);
+    rc = snn_iteration(S, tau, ni, st);
+    set.kernels[tau] = (int64_t)fhe::launches() - before;
+    fhe::note_launches(-set.kernels[tau]);
+    if (S->profile) set.pbs_counts[tau] = S->ev_count[tau];
     cudaError_t e = cudaStreamEndCapture(st, &graph);
-    if (rc) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
-    FHE_CUDA_TRY(e);
-    cudaError_t ie = cudaGraphInstantiate(&S->graphs[tau], graph, 0);
+    if (rc) { if (e == cudaSuccess) cudaGraphDestroy(graph); break; }
+    if (e != cudaSuccess) { (void)cudaGetLastError(); rc = FHE_ECUDA; break; }
+    cudaError_t ie = cudaGraphInstantiate(&set.execs[tau], graph, 0);
     cudaGraphDestroy(graph);
-    FHE_CUDA_TRY(ie);
+    if (ie != cudaSuccess) { (void)cudaGetLastError(); rc = FHE_ECUDA; }
   }
-  S->graph_images = ni;
+  if (rc) {
+    for (auto &g : set.execs)
+      if (g) cudaGraphExecDestroy(g);
+    return rc;
+  }
+  S->graphs[ni] = set;
   return FHE_OK;
 }
 
@@ -318,16 +337,18 @@ extern "C" int fhe_snn_step(fhe_snn *S, void *stream) {
   const size_t ni = S->cur_images;
   const uint32_t tau = S->next_iter;
   if (S->desc.use_graph & 1) {
-    if (S->graph_images != ni || S->graphs.size() != iters) {
+    if (S->graphs.find(ni) == S->graphs.end()) {
       FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
       FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
       int rc = snn_capture(S, ni, S->gs);
       if (rc) return rc;
     }
+    const fhe_snn::GraphSet &set = S->graphs[ni];
     FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
     FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
-    FHE_CUDA_TRY(cudaGraphLaunch(S->graphs[tau], S->gs));
-    fhe::note_launches(S->graph_kernels[tau]);
+    FHE_CUDA_TRY(cudaGraphLaunch(set.execs[tau], S->gs));
+    fhe::note_launches(set.kernels[tau]);
+    if (S->profile) S->ev_count[tau] = set.pbs_counts[tau];
     FHE_CUDA_TRY(cudaEventRecord(S->join_out, S->gs));
     FHE_CUDA_TRY(cudaStreamWaitEvent(st, S->join_out, 0));
   } else {

@@ -34,7 +34,7 @@ def main():
     lut = fhe.lut_create(keys, synth.identity_plus_threshold_lut(p)[None])
     macs = P["n"] * (P["k"] + 1) ** 2 * P["l"] * P["N"] ** 2
     for variant in args.variants.split(","):
-        v = fhe.VARIANT_TC if variant == "tc" else fhe.VARIANT_EXACT
+        v = {"exact": fhe.VARIANT_EXACT, "tc": fhe.VARIANT_TC, "fft": fhe.VARIANT_FFT}[variant]
         for batch in [int(b) for b in args.batches.split(",")]:
             msgs = synth.uniform_messages(args.seed + batch, batch, p)
             ct = fhe.encrypt(keys, msgs, seed=1000 + batch)
