@@ -218,15 +218,38 @@ int fhe_status(fhe_keys *keys, void *stream);
  *   x_next = S;  scores += S of the last layer.
  * The first layer's input is either static (pixel ciphertexts reused every
  * step, the conv output computed once) or a per-step spike train.
+ *
+ * FHE_LAYER_POISSON (first layer only, static input): the Poisson encoder of
+ * 2.3 (Eq. Poisson-coding), S[t] = [x > M_t] per pixel, where M_t is the
+ * server's public random matrix of step t (drawn by the caller); one
+ * comparison bootstrap per pixel and step (5.1, Table Poisson).  It has no
+ * WeightSum and no membrane: with FHE_LIF_MULTI_VALUE the comparison is the
+ * Fire table on x - M_t + V_th - 1 (>= V_th exactly when x > M_t); with
+ * FHE_LIF_TWO_PBS it is the sign bootstrap of x - M_t - 1, plus 1.
+ * Pixel levels and M_t must keep these inputs inside the table's range
+ * ([-p/2, p/2) resp. [-p, p)), as Thm 4.1 does for the LIF layers.
+ *
+ * lif_mode selects how one LIF neuron-step is bootstrapped:
+ *  FHE_LIF_MULTI_VALUE: one blind rotation of H + p/2 with a multi-value test
+ *    polynomial gives FHE-Fire and FHE-Reset (tables on v in [-p/2, p/2));
+ *  FHE_LIF_TWO_PBS: the paper's two bootstraps (4.2, Eq. FHE-Fire and
+ *    FHE-Reset) with negacyclic program functions, no centring:
+ *    S = bootstrap_sign(H - V_th) + 1 = 2 Spike, V = bootstrap_g(H), valid for
+ *    H in [V_th - p, p) (Thm 4.1 with the paper's modulus 2p).  Requires
+ *    spike_scale == 2 (the spike value the construction produces).
  */
 #define FHE_LAYER_FC 0
 #define FHE_LAYER_CONV 1
+#define FHE_LAYER_POISSON 2
+#define FHE_LIF_MULTI_VALUE 0
+#define FHE_LIF_TWO_PBS 1
 
 typedef struct fhe_layer_desc {
-  int32_t type;            /* FHE_LAYER_FC or FHE_LAYER_CONV                  */
-  const int32_t *weights;  /* HOST int32: FC [out][in]; conv [cout][cin][kh][kw] */
-  uint32_t in_size;        /* FC: number of inputs                           */
-  uint32_t out_size;       /* FC: number of outputs                          */
+  int32_t type;            /* FHE_LAYER_FC, FHE_LAYER_CONV or FHE_LAYER_POISSON */
+  const int32_t *weights;  /* HOST int32: FC [out][in]; conv [cout][cin][kh][kw];
+                              Poisson: thresholds M [T][in_size]              */
+  uint32_t in_size;        /* FC, Poisson: number of inputs                  */
+  uint32_t out_size;       /* FC: number of outputs; Poisson: = in_size      */
   uint32_t cin, h, w, cout, kh, kw, stride, pad; /* conv geometry          */
 } fhe_layer_desc;
 
@@ -243,14 +266,18 @@ typedef struct fhe_snn_desc {
   int32_t use_graph;            /* bit 0: capture each time step as a CUDA
                                    graph; bit 1 (FHE_SNN_PROFILE): time the
                                    blind rotations (fhe_snn_profile)        */
+  int32_t lif_mode;             /* FHE_LIF_MULTI_VALUE or FHE_LIF_TWO_PBS     */
 } fhe_snn_desc;
 
 /* Build a network on `keys` (uploads weights, allocates state for
- * max_images images; synchronous).  Errors: FHE_EINVAL, FHE_ENOMEM. */
+ * max_images images; synchronous).  Errors: FHE_EINVAL (bad geometry, a
+ * Poisson layer that is not the first or without static input, an unknown
+ * lif_mode, FHE_LIF_TWO_PBS with spike_scale != 2), FHE_ENOMEM. */
 int fhe_snn_create(fhe_keys *keys, const fhe_snn_desc *desc, fhe_snn **out);
 void fhe_snn_free(fhe_snn *net);
 
-/* Number of bootstraps (blind rotations) one inference of one image runs. */
+/* Number of bootstraps (blind rotations) one inference of one image runs:
+ * per step one per neuron (two per LIF neuron with FHE_LIF_TWO_PBS). */
 uint64_t fhe_snn_pbs_per_image(const fhe_snn *net);
 
 /* Encrypted inference of `n_images` images (<= max_images).

@@ -21,6 +21,8 @@ def max_abs_inputs(P, net, images):
     for img in images:
         res = O.snn_plain(P, net, img.reshape(-1))
         for li in range(len(net["layers"])):
+            if net["layers"][li]["type"] == "poisson":
+                continue  # no WeightSum, no membrane
             # I[t] = H[t] - V[t-1]; V[-1] = 0
             H = res["h"][li].astype(np.int64)
             V = np.zeros_like(H)
@@ -44,6 +46,25 @@ def calibrate(P=synth.P630, n_images=64, seed=1000):
     return tuple(divisors), worst
 
 
+def calibrate_poisson(P=synth.P630, n_images=16, seed=1000, T=20):
+    """Divisors of the Poisson-encoded network's two FC layers (the encoder
+    has no weights), on images quantised to POISSON_LEVELS levels."""
+    p = 1 << P["log2_p"]
+    images = synth.stroke_images(seed, n_images, levels=synth.POISSON_LEVELS)
+    v_th = synth.LIF_DEFAULT["v_th"]
+    divisors = [1, 1]
+    for li in (1, 2):
+        while True:
+            net = synth.poisson_fc_net(T=T, divisors=tuple(divisors))
+            worst = max_abs_inputs(P, net, images)
+            if v_th + worst[li] <= p // 2:
+                break
+            divisors[li - 1] += 1
+    return tuple(divisors), worst
+
+
 if __name__ == "__main__":
     d, w = calibrate()
     print("CSNN_DIVISORS =", d, "max|I| per layer =", w.tolist())
+    d, w = calibrate_poisson()
+    print("POISSON_DIVISORS =", d, "max|I| per layer =", w.tolist())

@@ -266,6 +266,17 @@ def lwe_add_const(P, ct, value):
     return ct
 
 
+def lwe_add_consts(P, ct, values):
+    """Trivial plaintext addition, one message per ciphertext: b_i += m_i * Delta
+    (mod 2^32), a unchanged (2.1: LWE is additively homomorphic)."""
+    w = P["n"] + 1
+    ct = np.array(ct, dtype=np.uint32, copy=True).reshape(-1, w)
+    m = (np.asarray(values, np.int64).reshape(-1) % (1 << 32)).astype(np.uint64)
+    b = (ct[:, -1].astype(np.uint64) + m * np.uint64(delta(P))) % np.uint64(1 << 32)
+    ct[:, -1] = b.astype(np.uint32)
+    return ct
+
+
 # ---------------------------------------------------------------- LIF (4.2)
 def lif_luts(P, v_th, leak_shift, spike_scale):
     """FHE-Fire and FHE-Reset program functions as LUTs over u in [0, p).
@@ -283,19 +294,42 @@ def lif_luts(P, v_th, leak_shift, spike_scale):
     return np.stack([fire, reset]).astype(np.int32)
 
 
+def lif_luts_two_pbs(P, v_th, leak_shift):
+    """The paper's two program functions for separate bootstraps (4.2), as
+    tables over u in [0, p); the bootstrap's negacyclic half gives -g(u) for
+    messages in [-p, 0) (the paper's plaintext modulus is 2p here, with
+    Delta = q / 2p, so g(v + p) = -g(v) holds by construction).
+
+    Sign (Eq. FHE-Fire): g = 1, so bootstrap(H - V_th) + 1 = 2 Spike.
+    Reset (Eq. FHE-Reset): 0 for u >= V_th, leak(u) for 0 <= u < V_th.
+    """
+    p = 1 << P["log2_p"]
+    u = np.arange(p, dtype=np.int64)
+    sign = np.ones(p, np.int64)
+    reset = np.where(u >= v_th, 0, u >> leak_shift)
+    return np.stack([sign, reset]).astype(np.int32)
+
+
+def poisson_spikes(x, M_t, spike):
+    """Poisson encoding (2.3, Eq. Poisson-coding): a spike of value `spike`
+    where the pixel exceeds the step's random value, none where it does not."""
+    return np.where(np.asarray(x, np.int64) > np.asarray(M_t, np.int64), spike, 0)
+
+
 def wrap2p(x, p):
     """Signed representative in [-p, p) of x mod 2p."""
     x = np.asarray(x, dtype=np.int64)
     return ((x + p) % (2 * p)) - p
 
 
-def plain_bootstrap(f, v, p):
-    """What a bootstrap of a message v (mod 2p, centred by +p/2) decrypts to.
+def plain_bootstrap(f, v, p, centre=True):
+    """What a bootstrap of a message v (mod 2p, centred by +p/2 unless
+    centre is False) decrypts to.
 
     u = (v + p/2) mod 2p; f(u) for u < p, -f(u - p) otherwise (negacyclic half,
     Thm 2.1), reduced mod 2p.
     """
-    u = (np.asarray(v, dtype=np.int64) + p // 2) % (2 * p)
+    u = (np.asarray(v, dtype=np.int64) + (p // 2 if centre else 0)) % (2 * p)
     f = np.asarray(f, dtype=np.int64)
     out = np.where(u < p, f[np.minimum(u, p - 1)], -f[np.maximum(u - p, 0)])
     return wrap2p(out, p)
@@ -330,11 +364,18 @@ def snn_plain(P, net, inputs):
     Returns dict(spikes=[per layer (T, size)], h=[per layer (T, size)],
     scores=(n_out,)).  H[t] = V[t-1] + I[t]; S = Fire(H); V = Reset(H);
     scores = sum_t S_last[t] (5.3, step 4).
+
+    net['lif_mode'] = 'two_pbs' evaluates the paper's separate negacyclic
+    bootstraps (4.2): S = sign(H - V_th) + 1, V = g(H) without centring.  A
+    'poisson' first layer (2.3) spikes where the pixel exceeds M[t]; its 'h'
+    entry is x - M[t].
     """
     p = 1 << P["log2_p"]
     T = net["T"]
     lif = net["lif"]
+    two = net.get("lif_mode") == "two_pbs"
     f = lif_luts(P, lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+    g = lif_luts_two_pbs(P, lif["v_th"], lif["leak_shift"])
     V = [None] * len(net["layers"])
     spikes = [[] for _ in net["layers"]]
     hs = [[] for _ in net["layers"]]
@@ -342,6 +383,12 @@ def snn_plain(P, net, inputs):
     for t in range(T):
         x = inputs if net.get("static_input") else inputs[t]
         for li, layer in enumerate(net["layers"]):
+            if layer["type"] == "poisson":
+                S = poisson_spikes(x, layer["M"][t], 2 if two else lif["spike_scale"])
+                spikes[li].append(S)
+                hs[li].append(np.asarray(x, np.int64) - np.asarray(layer["M"][t], np.int64))
+                x = S
+                continue
             if li == 0 and net.get("static_input"):
                 if static_I0 is None:
                     static_I0 = wrap2p(_plain_layer(layer, x), p)
@@ -351,8 +398,12 @@ def snn_plain(P, net, inputs):
             if V[li] is None:
                 V[li] = np.zeros_like(I)
             H = wrap2p(V[li] + I, p)
-            S = plain_bootstrap(f[0], H, p)
-            V[li] = plain_bootstrap(f[1], H, p)
+            if two:
+                S = wrap2p(plain_bootstrap(g[0], H - lif["v_th"], p, centre=False) + 1, p)
+                V[li] = plain_bootstrap(g[1], H, p, centre=False)
+            else:
+                S = plain_bootstrap(f[0], H, p)
+                V[li] = plain_bootstrap(f[1], H, p)
             spikes[li].append(S)
             hs[li].append(H)
             x = S
@@ -367,14 +418,20 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
     ct_inputs: (T, n_in, n+1) or (n_in, n+1) when static.  Per layer and step:
     I = WeightSum(x); H = V + I; (S, V) = bootstrap(H + p/2) with the two LIF
     LUTs (one blind rotation, multi-value); the last layer's spikes are summed
-    into the encrypted scores.  Returns dict(spikes=[per layer (T, size, n+1)],
-    scores=(n_out, n+1)).
+    into the encrypted scores.  With net['lif_mode'] = 'two_pbs':
+    S = bootstrap(H - V_th; sign) + 1 and V = bootstrap(H; g), no centring
+    (4.2).  A 'poisson' first layer bootstraps the comparison x > M[t] (2.3):
+    the Fire table on x - M[t] + V_th - 1 (multi-value; its Reset output is
+    not used) or the sign table on x - M[t] - 1, plus 1 (two bootstraps).
+    Returns dict(spikes=[per layer (T, size, n+1)], scores=(n_out, n+1)).
     """
     p = 1 << P["log2_p"]
     w = P["n"] + 1
     T = net["T"]
     lif = net["lif"]
+    two = net.get("lif_mode") == "two_pbs"
     luts = lif_luts(P, lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+    g = lif_luts_two_pbs(P, lif["v_th"], lif["leak_shift"])
     V = [None] * len(net["layers"])
     spikes = [[] for _ in net["layers"]]
     static_I0 = None
@@ -382,6 +439,17 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
     for t in range(T):
         x = ct_inputs if net.get("static_input") else ct_inputs[t]
         for li, layer in enumerate(net["layers"]):
+            if layer["type"] == "poisson":
+                M = np.asarray(layer["M"][t], np.int64)
+                if two:
+                    Hf = lwe_add_consts(P, x, -M - 1)
+                    S = lwe_add_const(P, pbs(P, keys, Hf, g[0:1], nthreads=nthreads)[0], 1)
+                else:
+                    Hc = lwe_add_consts(P, x, -M + lif["v_th"] - 1 + p // 2)
+                    S = pbs(P, keys, Hc, luts, nthreads=nthreads)[0]
+                spikes[li].append(S)
+                x = S
+                continue
             if li == 0 and net.get("static_input") and static_I0 is not None:
                 I = static_I0
             elif layer["type"] == "fc":
@@ -394,9 +462,14 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
             if V[li] is None:
                 V[li] = np.zeros_like(I)
             H = (V[li] + I).astype(np.uint32)
-            Hc = lwe_add_const(P, H, p // 2)
-            out = pbs(P, keys, Hc, luts, nthreads=nthreads)
-            S, V[li] = out[0], out[1]
+            if two:
+                Hf = lwe_add_const(P, H, -lif["v_th"])
+                S = lwe_add_const(P, pbs(P, keys, Hf, g[0:1], nthreads=nthreads)[0], 1)
+                V[li] = pbs(P, keys, H, g[1:2], nthreads=nthreads)[0]
+            else:
+                Hc = lwe_add_const(P, H, p // 2)
+                out = pbs(P, keys, Hc, luts, nthreads=nthreads)
+                S, V[li] = out[0], out[1]
             spikes[li].append(S)
             x = S
         scores = spikes[-1][-1].copy() if scores is None else (scores + spikes[-1][-1]).astype(np.uint32)

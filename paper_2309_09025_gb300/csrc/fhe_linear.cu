@@ -113,6 +113,20 @@ __global__ void k_lwe_add(uint32_t n, const uint32_t *a, const uint32_t *b, uint
   }
 }
 
+// out = a + (cst + offs[i % n_in] * delta) on b, per ciphertext i: a public
+// per-input plaintext added to every image's ciphertexts (the Poisson
+// encoder's thresholds, 2.3).
+__global__ void k_lwe_add_offsets(uint32_t n, const uint32_t *a, const int32_t *offs, uint32_t n_in,
+                                  uint32_t delta, uint32_t cst, uint64_t words, uint32_t *out) {
+  const uint32_t w = n + 1u;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < words;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = a[e];
+    if (e % w == n) v += cst + (uint32_t)offs[(e / w) % n_in] * delta;
+    out[e] = v;
+  }
+}
+
 }  // namespace
 
 extern "C" int fhe_lwe_linear(uint32_t n, uint32_t log2_p, const int32_t *W, size_t M, size_t K,
@@ -159,6 +173,17 @@ int lwe_add(uint32_t n, const uint32_t *a, const uint32_t *b, uint32_t cst, uint
   unsigned blocks = (unsigned)((words + 255u) / 256u);
   if (blocks > 152u * 32u) blocks = 152u * 32u;
   k_lwe_add<<<blocks, 256, 0, st>>>(n, a, b, cst, words, out);
+  note_launches(1);
+  FHE_CUDA_TRY(cudaGetLastError());
+  return FHE_OK;
+}
+int lwe_add_offsets(uint32_t n, const uint32_t *a, const int32_t *offs, uint32_t n_in,
+                    uint32_t delta, uint32_t cst, uint64_t count, uint32_t *out, cudaStream_t st) {
+  const uint64_t words = count * (n + 1u);
+  if (!words) return FHE_OK;
+  unsigned blocks = (unsigned)((words + 255u) / 256u);
+  if (blocks > 152u * 32u) blocks = 152u * 32u;
+  k_lwe_add_offsets<<<blocks, 256, 0, st>>>(n, a, offs, n_in, delta, cst, words, out);
   note_launches(1);
   FHE_CUDA_TRY(cudaGetLastError());
   return FHE_OK;

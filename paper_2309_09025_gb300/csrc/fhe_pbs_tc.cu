@@ -16,23 +16,31 @@
 // 2^24: the accumulator is drained (cvt to int32, shifted by 8L, added modulo
 // 2^32) after at most 2^24 / (Bg/2 * 128) terms.
 //
-// Operands (SWIZZLE_NONE, K-major, 8x8 fp16 core matrices of 128 bytes):
-//  - A = digits, M = 128 ciphertexts, tiles of 128 x 64 (LBO 128, SBO 1024);
-//    written once per step to global memory and multicast by cp.async.bulk to
-//    the four CTAs of the cluster (each CTA issues one quarter);
-//  - B = Hankel key, N = 256 output coefficients.  Core matrix delta holds
-//    h[8 delta + rho + kappa]; with LBO = SBO = 128 bytes the matrix
-//    descriptor walks one strip of core matrices for both the N and K
-//    directions, so one 20 KB window per (key row r, limb) feeds all 64 K16
-//    steps of a 256-coefficient block.
-//  - D = TMEM fp32, 128 lanes (ciphertexts) x 256 columns, double buffered.
+// Operands (SWIZZLE_NONE, K-major, 8x8 fp16 core matrices of 128 bytes), for
+// a CTA pair running tcgen05.mma.cta_group::2 with M = 256, N = 256, K = 16:
+//  - A = digits of 256 ciphertexts; each CTA holds its 128 rows in tiles of
+//    128 x 64 (LBO 128, SBO 1024).  Digits are written once per step to
+//    global memory and multicast by cp.async.bulk to the two CTAs (one per
+//    pair) that hold the same 128 rows; each of them sends the 64 rows it
+//    generated.
+//  - B = Hankel key, N = 256 output coefficients split 128 + 128 between the
+//    two CTAs of the pair.  Core matrix delta holds h[8 delta + rho + kappa];
+//    with LBO = SBO = 128 bytes the matrix descriptor walks one strip of core
+//    matrices for both the N and K directions, so one 18 KB window per
+//    (key row r, limb) feeds all 64 K16 steps of a 256-coefficient block.
+//  - D = TMEM fp32, 128 lanes (the CTA's ciphertexts) x 256 columns, double
+//    buffered (512 columns, allocated jointly by the pair).
+// Per SM, an M256 N256 K16 step of the pair reads 4 KB of A and 4 KB of B
+// from shared memory (64 B/clk at the tensor rate) instead of 4 + 8 KB for a
+// single-CTA M128 N256 step.
 //
-// Cluster of 4 CTAs (one per SM) = 128 ciphertexts.  CTA q owns output
-// polynomial j = q / 2, coefficients [512 (q % 2), +512) in two blocks of
-// 256, all limbs.  Per step: digits (all warps) -> cluster barrier -> units
-// (block, limb, chunk) run by a producer warp (bulk copies), an MMA warp and
-// eight epilogue warps (TMEM -> registers, limb recombination, ACC update in
-// global memory) -> cluster barrier.
+// Cluster of 4 CTAs = 2 pairs = 256 ciphertexts.  Pair j computes output
+// polynomial j (all N coefficients, 4 limbs) for all 256 ciphertexts.  Per
+// step: digits (all warps; each CTA makes the digits of 64 ciphertexts) ->
+// units (block, limb, chunk) run by a producer warp (bulk copies), the
+// leader's MMA warp (the peer's warp 1 relays "operand landed" to the
+// leader's barriers) and eight epilogue warps per CTA (TMEM -> registers,
+// limb recombination, ACC update in global memory) -> cluster barrier.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,14 +51,16 @@ using fhe::Params;
 
 namespace {
 
-constexpr int kCluster = 4;
-constexpr int kBt = 128;          // ciphertexts per cluster (MMA M)
+constexpr int kCluster = 4;       // two CTA pairs
+constexpr int kBt = 256;          // ciphertexts per cluster (MMA M of a CTA pair)
+constexpr int kBh = 128;          // ciphertexts per CTA (its half of M)
 constexpr int kBN = 256;          // output coefficients per block (MMA N)
 constexpr int kKB = 64;           // K elements per A tile
-// A-operand pipeline depth: 10 stages at N = 1024, 8 at N = 2048 (the B
-// windows grow with N; both fit in 227 KB of shared memory).
-__host__ __device__ constexpr uint32_t tc_stages(uint32_t N) { return N <= 1024u ? 10u : 8u; }
-constexpr int kATile = kBt * kKB * 2;   // 16 KB
+constexpr int kATile = kBh * kKB * 2;   // 16 KB: one CTA's 128 rows x 64 K
+constexpr uint32_t kAStages = 9;  // A-operand pipeline depth (9 x 16 KB)
+// One B window: the 128 columns of a CTA over K = 1024 of a Hankel strip,
+// (128 + 1024) / 8 core matrices of 128 bytes.
+constexpr uint32_t kBWin = (128u + 1024u) / 8u * 128u;
 constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
 constexpr int kTmemCols = 512;
 
@@ -69,9 +79,6 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
@@ -105,6 +112,13 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, vol
   }
   return true;
 }
+// Bounded wait that does not give up on the abort flag (used to drain the
+// tensor pipe before TMEM is released).
+__device__ __forceinline__ void wait_time_bounded(uint64_t *bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return;
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
                                          uint64_t *bar) {
   asm volatile(
@@ -127,25 +141,37 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_commit_multicast(uint64_t *bar, uint16_t mask) {
+// Completion of every tcgen05.mma this thread issued arrives on the barrier at
+// the same offset in each CTA of `mask`.
+__device__ __forceinline__ void tc2_commit_multicast(uint64_t *bar, uint16_t mask) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
       " [%0], %1;" ::"r"(smem_u32(bar)),
       "h"(mask)
       : "memory");
 }
-__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                           uint32_t idesc, uint32_t accumulate) {
+// D[256 x N] (+)= A[256 x 16] B[16 x N] over the CTA pair: rows 0..127 of A
+// and D live in the leader CTA, rows 128..255 in its peer; each CTA holds
+// N/2 columns of B; the descriptors give the same offsets in both CTAs.
+__device__ __forceinline__ void tc2_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+// Address of this CTA's shared variable `p` in the CTA of cluster rank `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+// Arrive on a barrier of another CTA of the cluster (default semantics; the
+// operands it announces were written by the async proxy and are read by the
+// tensor core, which the barrier phase alone orders).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -223,22 +249,25 @@ struct TcLut {
 struct TcSmem {
   uint32_t a, b, bars, tmem_slot, total;
 };
-__host__ __device__ inline TcSmem tc_smem(uint32_t N) {
+// A stages, then two B stages of two 128-column windows (one per limb of the
+// unit; each window covers K = 1024).  The B region also stages accumulators
+// during the digit phase (two buffers of 32 KB).
+__host__ __device__ inline TcSmem tc_smem() {
   TcSmem s;
   uint32_t o = 0;
-  s.a = o; o += tc_stages(N) * kATile;
-  s.b = o; o += 2u * ((kBN + N) / 8u) * 128u;
-  s.bars = o; o += 32u * 8u;
+  s.a = o; o += kAStages * kATile;
+  s.b = o; o += 2u * 2u * kBWin;
+  s.bars = o; o += 48u * 8u;   // 3 x 9 + 11 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
 }
 
-// Global scratch of one cluster tile: ACC [128][2][N] u32 then digits
-// [R][N/64 tiles][16 KB].
+// Global scratch of one cluster tile (256 ciphertexts): ACC [256][2][N] u32,
+// then digits [2 halves][RR rows][N/64 tiles][128 x 64] fp16.
 __host__ __device__ inline uint64_t tc_tile_acc_words(uint32_t N) { return (uint64_t)kBt * 2u * N; }
-__host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t R) {
-  return (uint64_t)R * (N / kKB) * (kATile / 2);
+__host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) {
+  return 2ull * RR * (N / kKB) * (kATile / 2);
 }
 
 template <int N>
@@ -249,58 +278,71 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                       uint32_t chunk_r, uint32_t sub_shift, uint32_t *__restrict__ big_out,
                       int *status) {
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
-  constexpr uint32_t kAStages = tc_stages(N);
-  constexpr uint32_t WIN = (kBN + N) / 8u;   // core matrices in one B window
-  constexpr uint32_t KBLK = N / kKB;         // A tiles per key row r
+  constexpr uint32_t KBLK = N / kKB;             // A tiles per digit row r
+  constexpr uint32_t KH = N / 1024u;             // B windows (K = 1024 each) per row
+  constexpr uint32_t TILE_H = kATile / 2;        // fp16 elements of one A tile
+  constexpr uint32_t G = 4096u / N;              // ciphertexts per staged group (32 KB)
+  constexpr uint32_t NGROUP = 64u / G;
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcSmem S = tc_smem(N);
+  const TcSmem S = tc_smem();
   unsigned char *sA = smem + S.a;
   unsigned char *sB = smem + S.b;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S.bars);
-  uint64_t *a_full = bars, *a_empty = bars + kAStages;
-  uint64_t *b_full = bars + 2 * kAStages, *b_empty = b_full + 2;
-  uint64_t *t_full = b_empty + 2, *t_empty = t_full + 2;
+  uint64_t *a_full = bars, *a_empty = bars + kAStages, *a_peer = bars + 2 * kAStages;
+  uint64_t *b_full = bars + 3 * kAStages, *b_empty = b_full + 2, *b_peer = b_full + 4;
+  uint64_t *t_full = b_full + 6, *t_empty = b_full + 7, *done = b_full + 8;
+  uint64_t *g_full = b_full + 9;  // two staging buffers of the digit phase
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
-  __shared__ uint32_t s_abar[32];  // a~_i of this CTA's 32 ciphertexts
+  __shared__ uint32_t s_abar[64];  // a~_i of the 64 ciphertexts whose digits this CTA makes
 
   const uint32_t n = P.n, l = P.l, R = 2u * l;
   const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
   const uint32_t q = cluster_rank();
+  const uint32_t pj = q / 2u;               // pair index = output polynomial j
+  const uint32_t hh = q % 2u;               // ciphertext half (MMA rows 128 hh ..)
+  const uint32_t lead = q & ~1u;            // rank of the pair's leader (issues the MMAs)
+  const bool leader = (hh == 0u);
   const uint64_t tile = blockIdx.x / kCluster;
   const size_t base = (size_t)tile * kBt;
-  uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);            // [128][2][N]
-  __half *dig = dig_g + tile * tc_tile_dig_halves(N, sub_shift ? 4u * l : 2u * l);
-  const uint32_t jq = q / 2u;                 // output polynomial of this CTA
-  const uint32_t cq = (q % 2u) * (N / 2u);    // first output coefficient
-  const uint32_t nblk = (N / 2u) / kBN;       // blocks of 256 per CTA
   // With sub_shift > 0 every gadget digit d is split into two signed
   // sub-digits d = hi * 2^sub_shift + lo (rows r and R + r of the digit
   // operand) so that each fp32 partial sum stays within 2^24; chunks never mix
   // low and high rows, and high rows are scaled by 2^sub_shift when drained.
   const uint32_t RR = sub_shift ? 2u * R : R;
+  uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);           // [256][2][N]
+  __half *dig = dig_g + tile * tc_tile_dig_halves(N, RR);
+  __half *dig_h = dig + (uint64_t)hh * RR * KBLK * TILE_H;        // this half's digit rows
+  const uint32_t row0 = kBh * hh + 64u * pj;  // first ciphertext whose digits this CTA makes
+  const uint32_t nblk = N / kBN;              // blocks of 256 output coefficients
   const uint32_t nchunk = RR / chunk_r;
   const uint64_t strip_halves = (uint64_t)(N / 4u) * 64u;
+  const uint16_t pair_mask = (uint16_t)(3u << lead);
+  const uint16_t a_mask = (uint16_t)((1u << q) | (1u << (q ^ 2u)));
 
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < kAStages; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], kCluster); }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1);
-      mbar_init(&t_full[s], 1); mbar_init(&t_empty[s], 8);
+    for (uint32_t s = 0; s < kAStages; ++s) {
+      mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 2); mbar_init(&a_peer[s], 1);
     }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); mbar_init(&b_peer[s], 1);
+      mbar_init(&g_full[s], 1);
+    }
+    mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    // collective over the CTA pair: the same 512 columns in both CTAs
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void *)tmem_slot)),
                  "r"((uint32_t)kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
-  // initial accumulators of this CTA's 32 ciphertexts: (0, X^{-b~} TV)
+  // initial accumulators of this CTA's 64 ciphertexts: (0, X^{-b~} TV)
   const uint32_t half_delta = P.delta() >> 1;
-  for (uint32_t e = tid; e < 32u * N; e += kThreads) {
-    const uint32_t b = 32u * q + e / N, c = e % N;
+  for (uint32_t e = tid; e < 64u * N; e += kThreads) {
+    const uint32_t b = row0 + e / N, c = e % N;
     const uint32_t v_ct = (base + b < count) ? ct_in[(base + b) * (n + 1u) + n] : 0u;
     const uint32_t bb = fhe::mod_switch_2n(v_ct, LOG2_2N);
     const uint32_t s = (c + bb) & (2u * N - 1u);
@@ -310,6 +352,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
     acc[((uint64_t)b * 2u + 0u) * N + c] = 0u;
     acc[((uint64_t)b * 2u + 1u) * N + c] = v;
   }
+  // generic stores of ACC are read by bulk copies (async proxy) in the digit phase
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -318,214 +362,262 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 
   const uint32_t total_bits = l * P.log2_bg;
   const uint32_t Bmask = (1u << P.log2_bg) - 1u, Bhalf = 1u << (P.log2_bg - 1u);
-  constexpr uint32_t idesc = idesc_f16(kBt, kBN);
-  // pipeline state (persistent across steps)
-  uint32_t a_it = 0, b_it = 0, u_it = 0;
+  constexpr uint32_t idesc = idesc_f16(2u * kBh, kBN);
+  // pipeline positions (each role advances the ones it uses)
+  uint32_t a_it = 0, b_it = 0, u_it = 0, g_it = 0;
 
   for (uint32_t i = 0; i < n; ++i) {
-    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 32 ciphertexts.
-    // One warp per chunk of 256 coefficients of one polynomial; lane L owns
-    // coefficients c = c_base + 32k + L (k < 8), so every load and store
-    // instruction of the warp is coalesced (the reversed index t' = N-1-c of
-    // 32 consecutive c spans four 16-byte core-matrix rows).
-    if (tid < 32u) {
-      const uint32_t b = 32u * q + tid;
+    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 64 ciphertexts.
+    // Groups of G ciphertexts (both polynomials, 32 KB) are staged in shared
+    // memory by bulk copies, double buffered.  One warp per chunk of 256
+    // coefficients of one polynomial; lane L owns c = c_base + 32k + L, so
+    // shared-memory reads are conflict free and global stores coalesced.
+    if (tid < 64u) {
+      const uint32_t b = row0 + tid;
       const uint32_t av = (base + b < count) ? __ldg(ct_in + (base + b) * (n + 1u) + i) : 0u;
       s_abar[tid] = fhe::mod_switch_2n(av, LOG2_2N);
     }
-    __syncthreads();
-    constexpr uint32_t CHUNKS = 32u * 2u * (N / 256u);
-    for (uint32_t chunk = warp; chunk < CHUNKS; chunk += kThreads / 32u) {
-      const uint32_t cb = chunk % (N / 256u), j = (chunk / (N / 256u)) & 1u;
-      const uint32_t bl = chunk / (2u * (N / 256u));  // row within this CTA's 32
-      const uint32_t b = 32u * q + bl;
-      const uint32_t a = s_abar[bl];
-      const uint32_t *Pj = acc + ((uint64_t)b * 2u + j) * N;
-      uint32_t xr[8];
-#pragma unroll
-      for (uint32_t k = 0; k < 8u; ++k) {
-        const uint32_t c = cb * 256u + 32u * k + lane;
-        const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
-        const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
-        xr[k] = rot - Pj[c];
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (uint32_t g = 0; g < 2u; ++g) {
+        mbar_expect_tx(&g_full[(g_it + g) & 1u], 32768u);
+        bulk_g2s(sB + ((g_it + g) & 1u) * 32768u, acc + (uint64_t)(row0 + g * G) * 2u * N, 32768u,
+                 &g_full[(g_it + g) & 1u]);
       }
-#pragma unroll
-      for (uint32_t k = 0; k < 8u; ++k)
-        xr[k] = (total_bits >= 32u)
-                    ? xr[k]
-                    : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
-      // least significant level first (carries propagate upwards)
-      for (int lam = (int)l - 1; lam >= 0; --lam) {
-        const uint32_t r = j * l + (uint32_t)lam;
+    }
+    __syncthreads();
+    for (uint32_t g = 0; g < NGROUP; ++g, ++g_it) {
+      const uint32_t buf = g_it & 1u;
+      const bool got = wait_bounded(&g_full[buf], (g_it >> 1) & 1u, &s_abort);
+      const uint32_t *sacc = reinterpret_cast<const uint32_t *>(sB + buf * 32768u);
+      constexpr uint32_t CH = G * 2u * (N / 256u);  // = 32 chunks of 256
+      for (uint32_t chunk = warp; got && chunk < CH; chunk += kThreads / 32u) {
+        const uint32_t cb = chunk % (N / 256u), j = (chunk / (N / 256u)) & 1u;
+        const uint32_t gi = chunk / (2u * (N / 256u));
+        const uint32_t bl = g * G + gi;             // 0..63
+        const uint32_t bm = 64u * pj + bl;          // MMA row within this half
+        const uint32_t a = s_abar[bl];
+        const uint32_t *Pj = sacc + (gi * 2u + j) * N;
+        uint32_t xr[8];
 #pragma unroll
         for (uint32_t k = 0; k < 8u; ++k) {
-          const uint32_t d = xr[k] & Bmask;
-          xr[k] >>= P.log2_bg;
-          int32_t sd = (int32_t)d;
-          if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
-          const uint32_t tp = N - 1u - (cb * 256u + 32u * k + lane);  // reversed index t'
-          const uint32_t in_tile = (b / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (b % 8u) * 8u + (tp % 8u);
-          if (sub_shift == 0u) {
-            dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(sd);
-          } else {
-            const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
-            int32_t lo = (int32_t)((uint32_t)sd & sm);
-            if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
-            const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
-            dig[(uint64_t)(r * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(lo);
-            dig[(uint64_t)((R + r) * KBLK + tp / 64u) * (kATile / 2) + in_tile] = __int2half_rn(hi);
+          const uint32_t c = cb * 256u + 32u * k + lane;
+          const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
+          const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
+          xr[k] = rot - Pj[c];
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 8u; ++k)
+          xr[k] = (total_bits >= 32u)
+                      ? xr[k]
+                      : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
+        // least significant level first (carries propagate upwards)
+        for (int lam = (int)l - 1; lam >= 0; --lam) {
+          const uint32_t r = j * l + (uint32_t)lam;
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k) {
+            const uint32_t d = xr[k] & Bmask;
+            xr[k] >>= P.log2_bg;
+            int32_t sd = (int32_t)d;
+            if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
+            const uint32_t tp = N - 1u - (cb * 256u + 32u * k + lane);  // reversed index t'
+            const uint32_t in_tile = (bm / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (bm % 8u) * 8u + (tp % 8u);
+            if (sub_shift == 0u) {
+              dig_h[(uint64_t)(r * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(sd);
+            } else {
+              const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
+              int32_t lo = (int32_t)((uint32_t)sd & sm);
+              if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
+              const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
+              dig_h[(uint64_t)(r * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(lo);
+              dig_h[(uint64_t)((R + r) * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(hi);
+            }
           }
         }
       }
+      __syncthreads();  // buffer `buf` is free again
+      if (tid == 0 && g + 2u < NGROUP && !s_abort) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&g_full[buf], 32768u);
+        bulk_g2s(sB + buf * 32768u, acc + (uint64_t)(row0 + (g + 2u) * G) * 2u * N, 32768u, &g_full[buf]);
+      }
     }
-    // The digits this CTA multicasts are the ones it just wrote (rows 32q..);
-    // a CTA-wide barrier orders them before its producer's bulk copies.
+    // This CTA multicasts exactly the digit rows it just wrote; a CTA-wide
+    // barrier orders them (and the staging buffers' last reads) before its
+    // producer's bulk copies.
     asm volatile("fence.proxy.async;" ::: "memory");
     __syncthreads();
 
-    // ---- external product units: (block, limb, chunk)
+    // ---- external product units (block, limb pair, chunk) of output
+    // polynomial pj: each A tile feeds both limbs of the pair (accumulators
+    // in TMEM columns 0..255 and 256..511).
     if (warp == 0) {
       if (lane == 0) {
         for (uint32_t blk = 0; blk < nblk; ++blk) {
-          const uint32_t c0 = cq + blk * kBN;
-          for (uint32_t L = 0; L < 4u; ++L)
+          const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
+          for (uint32_t lp = 0; lp < 2u; ++lp)
             for (uint32_t ch = 0; ch < nchunk; ++ch)
-              for (uint32_t rr = 0; rr < chunk_r; ++rr) {
-                const uint32_t r = ch * chunk_r + rr;
-                const uint32_t bs = b_it & 1u;
-                if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
-                if (!s_abort) {
-                  const __half *src = strips + ((((uint64_t)i * R + r % R) * 2u + jq) * 4u + L) * strip_halves +
-                                      (uint64_t)(c0 / 8u) * 64u;
-                  mbar_expect_tx(&b_full[bs], WIN * 128u);
-                  bulk_g2s(sB + bs * WIN * 128u, src, WIN * 128u, &b_full[bs]);
-                }
-                ++b_it;
-                for (uint32_t kb = 0; kb < KBLK; ++kb) {
-                  const uint32_t as = a_it % kAStages;
-                  if (a_it >= kAStages)
-                    wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
+              for (uint32_t rr = 0; rr < chunk_r; ++rr)
+                for (uint32_t kh = 0; kh < KH; ++kh) {
+                  const uint32_t r = ch * chunk_r + rr;
+                  const uint32_t bs = b_it & 1u;
+                  if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
                   if (!s_abort) {
-                    const __half *src = dig + (uint64_t)(r * KBLK + kb) * (kATile / 2) + q * (kATile / 8);
-                    mbar_expect_tx(&a_full[as], kATile);
-                    bulk_g2s_multicast(sA + as * kATile + q * (kATile / 4), src, kATile / 4,
-                                       &a_full[as], (uint16_t)((1u << kCluster) - 1u));
+                    mbar_expect_tx(&b_full[bs], 2u * kBWin);
+                    for (uint32_t z = 0; z < 2u; ++z) {
+                      const __half *src = strips +
+                                          ((((uint64_t)i * R + r % R) * 2u + pj) * 4u + 2u * lp + z) * strip_halves +
+                                          (uint64_t)((c0 + 1024u * kh) / 8u) * 64u;
+                      bulk_g2s(sB + (bs * 2u + z) * kBWin, src, kBWin, &b_full[bs]);
+                    }
                   }
-                  ++a_it;
+                  ++b_it;
+                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                    const uint32_t as = a_it % kAStages;
+                    if (a_it >= kAStages)
+                      wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
+                    if (!s_abort) {
+                      const __half *src = dig_h + (uint64_t)(r * KBLK + 16u * kh + kb) * TILE_H + pj * (TILE_H / 2u);
+                      mbar_expect_tx(&a_full[as], kATile);
+                      bulk_g2s_multicast(sA + as * kATile + pj * (kATile / 2), src, kATile / 2,
+                                         &a_full[as], a_mask);
+                    }
+                    ++a_it;
+                  }
                 }
-              }
         }
       }
       __syncwarp();
     } else if (warp == 1) {
-      if (lane == 0) {
+      if (lane == 0 && leader) {
         for (uint32_t blk = 0; blk < nblk; ++blk)
-          for (uint32_t L = 0; L < 4u; ++L)
+          for (uint32_t lp = 0; lp < 2u; ++lp)
             for (uint32_t ch = 0; ch < nchunk; ++ch) {
-              const uint32_t buf = u_it & 1u;
-              if (u_it >= 2u) wait_bounded(&t_empty[buf], ((u_it >> 1) - 1u) & 1u, &s_abort);
+              if (u_it >= 1u) wait_bounded(t_empty, (u_it - 1u) & 1u, &s_abort);
               tc_fence_after();
-              const uint32_t d_tmem = tmem + buf * (uint32_t)kBN;
               uint32_t accum = 0;
-              for (uint32_t rr = 0; rr < chunk_r; ++rr) {
-                const uint32_t bs = b_it & 1u;
-                wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort);
-                const uint32_t bbase = smem_u32(sB + bs * WIN * 128u);
-                for (uint32_t kb = 0; kb < KBLK; ++kb) {
-                  const uint32_t as = a_it % kAStages;
-                  wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
-                  tc_fence_after();
-                  if (!s_abort) {
-                    const uint32_t abase = smem_u32(sA + as * kATile);
+              for (uint32_t rr = 0; rr < chunk_r; ++rr)
+                for (uint32_t kh = 0; kh < KH; ++kh) {
+                  const uint32_t bs = b_it & 1u;
+                  wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort);
+                  wait_bounded(&b_peer[bs], (b_it >> 1) & 1u, &s_abort);
+                  const uint32_t bbase = smem_u32(sB + bs * 2u * kBWin);
+                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                    const uint32_t as = a_it % kAStages;
+                    wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
+                    wait_bounded(&a_peer[as], (a_it / kAStages) & 1u, &s_abort);
+                    tc_fence_after();
+                    if (!s_abort) {
+                      const uint32_t abase = smem_u32(sA + as * kATile);
 #pragma unroll
-                    for (uint32_t s = 0; s < 4u; ++s) {
-                      const uint64_t ad = smem_desc(abase + s * 256u, 128u, 1024u);
-                      const uint64_t bd = smem_desc(bbase + (8u * kb + 2u * s) * 128u, 128u, 128u);
-                      tc_mma_f16(d_tmem, ad, bd, idesc, accum);
-                      accum = 1u;
+                      for (uint32_t s = 0; s < 4u; ++s) {
+                        const uint64_t ad = smem_desc(abase + s * 256u, 128u, 1024u);
+#pragma unroll
+                        for (uint32_t z = 0; z < 2u; ++z) {
+                          const uint64_t bd = smem_desc(bbase + z * kBWin + (8u * kb + 2u * s) * 128u, 128u, 128u);
+                          tc2_mma_f16(tmem + z * (uint32_t)kBN, ad, bd, idesc, accum);
+                        }
+                        accum = 1u;
+                      }
+                      tc2_commit_multicast(&a_empty[as], (uint16_t)0xFu);
                     }
-                    tc_commit_multicast(&a_empty[as], (uint16_t)((1u << kCluster) - 1u));
+                    ++a_it;
                   }
-                  ++a_it;
+                  if (!s_abort) tc2_commit_multicast(&b_empty[bs], pair_mask);
+                  ++b_it;
                 }
-                if (!s_abort) tc_commit(&b_empty[bs]);
-                ++b_it;
-              }
-              if (!s_abort) tc_commit(&t_full[buf]);
+              if (!s_abort) tc2_commit_multicast(t_full, pair_mask);
               ++u_it;
             }
+      } else if (lane == 0) {
+        // peer: tell the leader when this CTA's halves of A and B have landed
+        const uint32_t bp0 = cluster_addr(&b_peer[0], lead), bp1 = cluster_addr(&b_peer[1], lead);
+        for (uint32_t blk = 0; blk < nblk; ++blk)
+          for (uint32_t lp = 0; lp < 2u; ++lp)
+            for (uint32_t ch = 0; ch < nchunk; ++ch)
+              for (uint32_t rr = 0; rr < chunk_r; ++rr)
+                for (uint32_t kh = 0; kh < KH; ++kh) {
+                  const uint32_t bs = b_it & 1u;
+                  if (wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort))
+                    mbar_arrive_remote(bs ? bp1 : bp0);
+                  ++b_it;
+                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                    const uint32_t as = a_it % kAStages;
+                    if (wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort))
+                      mbar_arrive_remote(cluster_addr(&a_peer[as], lead));
+                    ++a_it;
+                  }
+                }
       }
       __syncwarp();
     } else {
-      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 and columns
-      // 128 * ((w - 2) / 4) .. +128 of each 256-column buffer
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (ciphertexts) and
+      // columns 128 ((w - 2) / 4) .. +128 of both 256-column accumulators
       const uint32_t quarter = warp % 4u, half = (warp - 2u) / 4u;
-      const uint32_t b = 32u * quarter + lane;  // ciphertext row of the tile
+      const uint32_t row = kBh * hh + 32u * quarter + lane;  // ciphertext row of the tile
+      const uint32_t te = cluster_addr(t_empty, lead);
       for (uint32_t blk = 0; blk < nblk; ++blk) {
+        uint32_t *dst = acc + ((uint64_t)row * 2u + pj) * N + blk * kBN + half * 128u;
         uint32_t outv[128];
+        // ACC of this block, loaded while the block's MMAs run
 #pragma unroll
-        for (int k = 0; k < 128; ++k) outv[k] = 0u;
-        for (uint32_t L = 0; L < 4u; ++L)
+        for (int k = 0; k < 128; k += 4) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(dst + k);
+          outv[k] = v.x; outv[k + 1] = v.y; outv[k + 2] = v.z; outv[k + 3] = v.w;
+        }
+        for (uint32_t lp = 0; lp < 2u; ++lp)
           for (uint32_t ch = 0; ch < nchunk; ++ch) {
-            const uint32_t buf = u_it & 1u;
-            const uint32_t shift = 8u * L + ((ch * chunk_r >= R) ? sub_shift : 0u);
-            const bool got = wait_bounded(&t_full[buf], (u_it >> 1) & 1u, &s_abort);
+            const uint32_t sub = (ch * chunk_r >= R) ? sub_shift : 0u;
+            const bool got = wait_bounded(t_full, u_it & 1u, &s_abort);
             const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
             tc_fence_after();
             if (ok) {
-              const uint32_t tbase = tmem + ((32u * quarter) << 16) + buf * (uint32_t)kBN + half * 128u;
+#pragma unroll 1
+              for (uint32_t z = 0; z < 2u; ++z) {
+                const uint32_t shift = 8u * (2u * lp + z) + sub;
+                const uint32_t tbase = tmem + ((32u * quarter) << 16) + z * (uint32_t)kBN + half * 128u;
 #pragma unroll
-              for (uint32_t part = 0; part < 4u; ++part) {
-                uint32_t r[32];
-                tc_ld32(tbase + part * 32u, r);
+                for (uint32_t part = 0; part < 4u; ++part) {
+                  uint32_t r[32];
+                  tc_ld32(tbase + part * 32u, r);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                  const int32_t v = __float2int_rn(__uint_as_float(r[k]));
-                  outv[part * 32 + k] += (uint32_t)v << shift;
+                  for (int k = 0; k < 32; ++k) {
+                    const int32_t v = __float2int_rn(__uint_as_float(r[k]));
+                    outv[part * 32 + k] += (uint32_t)v << shift;
+                  }
                 }
               }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&t_empty[buf]);
+            if (lane == 0) mbar_arrive_remote(te);
             ++u_it;
           }
         if (!__any_sync(0xffffffffu, s_abort != 0)) {
-          const uint32_t c0 = cq + blk * kBN + half * 128u;
-          uint32_t *dst = acc + ((uint64_t)b * 2u + jq) * N + c0;
 #pragma unroll
-          for (int k0 = 0; k0 < 128; k0 += 16) {  // 4 loads in flight, then the stores
-            uint4 v[4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) v[m] = *reinterpret_cast<const uint4 *>(dst + k0 + 4 * m);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int k = k0 + 4 * m;
-              v[m].x += outv[k]; v[m].y += outv[k + 1]; v[m].z += outv[k + 2]; v[m].w += outv[k + 3];
-              *reinterpret_cast<uint4 *>(dst + k) = v[m];
-            }
-          }
+          for (int k = 0; k < 128; k += 4)
+            *reinterpret_cast<uint4 *>(dst + k) = make_uint4(outv[k], outv[k + 1], outv[k + 2], outv[k + 3]);
         }
       }
-    }
-    // keep every warp's iteration counters in step (only the issuing lanes and
-    // the epilogue advanced their own copies)
-    {
-      const uint32_t per_step_r = nblk * 4u * nchunk * chunk_r;
-      const uint32_t a_step = per_step_r * KBLK, u_step = nblk * 4u * nchunk;
-      if (warp == 0) { if (lane != 0) { a_it += a_step; b_it += per_step_r; } u_it += u_step; }
-      else if (warp == 1) { if (lane != 0) { a_it += a_step; b_it += per_step_r; u_it += u_step; } }
-      else { a_it += a_step; b_it += per_step_r; }
+      // the next step's digit phase reads ACC through bulk copies
+      asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     cluster_sync_all();
+  }
+
+  // Every MMA of the pair has completed before TMEM is released (on the
+  // normal path the epilogue already waited for all of them).
+  if (warp == 1 && lane == 0 && leader) {
+    tc2_commit_multicast(done, (uint16_t)(1u << q));
+    wait_time_bounded(done, 0u);
   }
 
   // ---- sample extraction (with the multi-value split when L == 2)
   const uint32_t W = N + 1u;
   for (uint32_t jl = 0; jl < lut.L; ++jl) {
     const uint32_t nnz = jl ? lut.nnz1 : lut.nnz0, off = jl ? lut.off1 : lut.off0;
-    for (uint32_t e = tid; e < 32u * W; e += kThreads) {
-      const uint32_t b = 32u * q + e / W, c = e % W;
+    for (uint32_t e = tid; e < 64u * W; e += kThreads) {
+      const uint32_t b = row0 + e / W, c = e % W;
       if (base + b >= count) continue;
       const uint32_t *A = acc + ((uint64_t)b * 2u) * N;
       const uint32_t *B = acc + ((uint64_t)b * 2u + 1u) * N;
@@ -548,9 +640,10 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)kTmemCols));
   }
   if (tid == 0 && s_abort) atomicExch(status, FHE_ETIMEOUT);
@@ -630,7 +723,7 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
   la.off0 = lut->off[0]; la.off1 = lut->off[1];
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
-  const TcSmem S = tc_smem(P.N);
+  const TcSmem S = tc_smem();
   auto kern = (P.N == 1024u) ? k_blind_rotate_tc<1024> : k_blind_rotate_tc<2048>;
   FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {

@@ -3,7 +3,10 @@
 //
 // Per layer l and time step t:  I = WeightSum(x);  H = V + I + (p/2) Delta;
 // (S, V) = bootstrap(H) with the Fire and Reset tables from ONE blind rotation
-// (multi-value split);  x_next = S;  scores += S of the last layer.
+// (multi-value split);  x_next = S;  scores += S of the last layer.  In the
+// two-bootstrap mode (4.2 as printed) S = bootstrap_sign(V + I - V_th) + 1 and
+// V = bootstrap_g(V + I) with negacyclic tables and no centring.  A Poisson
+// encoder first layer (2.3) bootstraps the comparison x > M_t per pixel.
 //
 // Layer-skewed schedule.  Layer l at step t only needs layer l-1 at step t
 // and itself at step t-1, so iteration tau runs every layer l with
@@ -23,15 +26,17 @@
 namespace fhe {
 int lwe_add(uint32_t n, const uint32_t *a, const uint32_t *b, uint32_t cst, uint64_t count,
             uint32_t *out, cudaStream_t st);
+int lwe_add_offsets(uint32_t n, const uint32_t *a, const int32_t *offs, uint32_t n_in,
+                    uint32_t delta, uint32_t cst, uint64_t count, uint32_t *out, cudaStream_t st);
 }
 
 namespace {
 struct Layer {
   int type;
-  int32_t *d_w;
+  int32_t *d_w;   // weights; Poisson: thresholds M [T][in_size]
   uint32_t in_size, out_size;
   uint32_t cin, h, w, cout, kh, kw, stride, pad;
-  uint32_t *d_I;  // [max_images][out][n+1]
+  uint32_t *d_I;  // [max_images][out][n+1] (not used by a Poisson layer)
 };
 }  // namespace
 
@@ -39,10 +44,14 @@ struct fhe_snn {
   fhe_keys *K;
   fhe_snn_desc desc;
   std::vector<Layer> layers;
-  fhe_lut *lut;
+  int mode;               // FHE_LIF_MULTI_VALUE or FHE_LIF_TWO_PBS
+  fhe_lut *lut;           // multi-value: Fire and Reset tables (L = 2)
+  fhe_lut *lut_fire;      // two bootstraps: sign table (L = 1)
+  fhe_lut *lut_reset;     // two bootstraps: reset table (L = 1)
   uint32_t n_in, n_out;
   uint64_t neurons;    // sum of the layers' sizes (per image)
   uint32_t *d_H;       // bootstrap inputs, all layers: [max_images * neurons][n+1]
+  uint32_t *d_Hf;      // two bootstraps: Fire inputs H - V_th, same layout
   uint32_t *d_out;     // [2][max_images * neurons][n+1]: spikes, then membrane V
   uint32_t *d_input;   // staging copy of the caller's input
   uint32_t *d_scores;  // [max_images][n_out][n+1]
@@ -50,7 +59,7 @@ struct fhe_snn {
   size_t cur_images;
   uint32_t next_iter;
   // captured graphs per batch size: one executable graph per iteration, its
-  // kernel-node count and its bracketed bootstrap count
+  // kernel-node count and its bracketed bootstrap counts (two per iteration)
   struct GraphSet {
     std::vector<cudaGraphExec_t> execs;
     std::vector<int64_t> kernels;
@@ -63,10 +72,10 @@ struct fhe_snn {
   cudaStream_t gs;
   cudaEvent_t join_in, join_out;
   size_t last_images;
-  // instrumentation: one event pair per iteration's bootstrap launch
+  // instrumentation: one event pair per bootstrap launch of an iteration
   bool profile;
-  std::vector<cudaEvent_t> ev;   // [iterations][2]
-  std::vector<size_t> ev_count;  // ciphertexts of each bracketed launch
+  std::vector<cudaEvent_t> ev;   // [iterations][2 launches][2]
+  std::vector<size_t> ev_count;  // [iterations][2]: ciphertexts of each bracketed launch
 };
 
 static uint32_t snn_iterations(const fhe_snn *S) {
@@ -88,10 +97,13 @@ static void snn_release(fhe_snn *S) {
     cudaFree(L.d_I);
   }
   cudaFree(S->d_H);
+  cudaFree(S->d_Hf);
   cudaFree(S->d_out);
   cudaFree(S->d_input);
   cudaFree(S->d_scores);
   fhe_lut_free(S->lut);
+  fhe_lut_free(S->lut_fire);
+  fhe_lut_free(S->lut_reset);
   delete S;
 }
 
@@ -101,6 +113,8 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   if (d->variant != FHE_VARIANT_EXACT && d->variant != FHE_VARIANT_TC &&
       d->variant != FHE_VARIANT_FFT)
     return FHE_EINVAL;
+  if (d->lif_mode != FHE_LIF_MULTI_VALUE && d->lif_mode != FHE_LIF_TWO_PBS) return FHE_EINVAL;
+  if (d->lif_mode == FHE_LIF_TWO_PBS && d->spike_scale != 2) return FHE_EINVAL;
   *out = NULL;
   const fhe::Params &P = K->P;
   const int32_t p = (int32_t)P.p();
@@ -108,16 +122,29 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   S->K = K;
   S->desc = *d;
   S->desc.layers = NULL;
-  // LIF tables on the centred input u = H + p/2, v = u - p/2 (Thm 3.2 / 4.2)
-  std::vector<int32_t> f(2u * (size_t)p);
-  for (int32_t u = 0; u < p; ++u) {
-    const int32_t v = u - p / 2;
-    f[u] = (v >= d->v_th) ? d->spike_scale : 0;
-    f[p + u] = (v >= d->v_th) ? 0 : (v >= 0 ? (v >> d->leak_shift) : 0);
-  }
+  S->mode = d->lif_mode;
   int rc = fhe::pbs_prepare(K, d->variant);
   if (rc) { snn_release(S); return rc; }
-  rc = fhe_lut_create(K, f.data(), 2u, &S->lut);
+  std::vector<int32_t> f(2u * (size_t)p);
+  if (S->mode == FHE_LIF_MULTI_VALUE) {
+    // LIF tables on the centred input u = H + p/2, v = u - p/2 (Thm 3.2 / 4.2)
+    for (int32_t u = 0; u < p; ++u) {
+      const int32_t v = u - p / 2;
+      f[u] = (v >= d->v_th) ? d->spike_scale : 0;
+      f[p + u] = (v >= d->v_th) ? 0 : (v >= 0 ? (v >> d->leak_shift) : 0);
+    }
+    rc = fhe_lut_create(K, f.data(), 2u, &S->lut);
+  } else {
+    // Negacyclic program functions on u in [0, p) (4.2); the bootstrap gives
+    // -g(u) on the other half [-p, 0).  Sign: g = 1.  Reset: 0 from V_th up,
+    // leak(u) below.
+    for (int32_t u = 0; u < p; ++u) {
+      f[u] = 1;
+      f[p + u] = (u >= d->v_th) ? 0 : (u >> d->leak_shift);
+    }
+    rc = fhe_lut_create(K, f.data(), 1u, &S->lut_fire);
+    if (!rc) rc = fhe_lut_create(K, f.data() + p, 1u, &S->lut_reset);
+  }
   if (rc) { snn_release(S); return rc; }
   uint32_t prev = 0;
   const uint32_t W = P.n + 1u;
@@ -130,6 +157,10 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
     if (ld.type == FHE_LAYER_FC) {
       L.in_size = ld.in_size; L.out_size = ld.out_size;
       wcount = (size_t)ld.in_size * ld.out_size;
+    } else if (ld.type == FHE_LAYER_POISSON) {
+      if (i != 0 || !d->static_input || ld.out_size != ld.in_size) { snn_release(S); return FHE_EINVAL; }
+      L.in_size = L.out_size = ld.in_size;
+      wcount = (size_t)d->T * ld.in_size;
     } else if (ld.type == FHE_LAYER_CONV) {
       if (!ld.stride || !ld.kh || !ld.kw || ld.h + 2 * ld.pad < ld.kh || ld.w + 2 * ld.pad < ld.kw) {
         snn_release(S); return FHE_EINVAL;
@@ -151,7 +182,8 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
     S->neurons += L.out_size;
     const size_t cts = (size_t)d->max_images * L.out_size;
     bool ok = cudaMalloc(&L.d_w, sizeof(int32_t) * wcount) == cudaSuccess &&
-              cudaMalloc(&L.d_I, sizeof(uint32_t) * cts * W) == cudaSuccess;
+              (L.type == FHE_LAYER_POISSON ||
+               cudaMalloc(&L.d_I, sizeof(uint32_t) * cts * W) == cudaSuccess);
     S->layers.push_back(L);
     if (!ok) { snn_release(S); return FHE_ENOMEM; }
     if (cudaMemcpy(L.d_w, ld.weights, sizeof(int32_t) * wcount, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -163,6 +195,7 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   const size_t all = (size_t)d->max_images * S->neurons;
   const size_t in_words = (size_t)d->max_images * (d->static_input ? 1u : d->T) * S->n_in * W;
   if (cudaMalloc(&S->d_H, sizeof(uint32_t) * all * W) != cudaSuccess ||
+      (S->mode == FHE_LIF_TWO_PBS && cudaMalloc(&S->d_Hf, sizeof(uint32_t) * all * W) != cudaSuccess) ||
       cudaMalloc(&S->d_out, sizeof(uint32_t) * 2u * all * W) != cudaSuccess ||
       cudaMalloc(&S->d_input, sizeof(uint32_t) * in_words) != cudaSuccess ||
       cudaMalloc(&S->d_scores, sizeof(uint32_t) * (size_t)d->max_images * S->n_out * W) != cudaSuccess) {
@@ -175,8 +208,8 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   }
   S->profile = (d->use_graph & FHE_SNN_PROFILE) != 0;
   if (S->profile) {
-    S->ev.assign((size_t)snn_iterations(S) * 2u, (cudaEvent_t)0);
-    S->ev_count.assign(snn_iterations(S), 0);
+    S->ev.assign((size_t)snn_iterations(S) * 4u, (cudaEvent_t)0);
+    S->ev_count.assign((size_t)snn_iterations(S) * 2u, 0);
     for (auto &e : S->ev)
       if (cudaEventCreate(&e) != cudaSuccess) { snn_release(S); return FHE_ECUDA; }
   }
@@ -192,7 +225,11 @@ extern "C" void fhe_snn_free(fhe_snn *S) {
 
 extern "C" uint64_t fhe_snn_pbs_per_image(const fhe_snn *S) {
   if (!S) return 0;
-  return S->neurons * S->desc.T;
+  uint64_t per_step = 0;
+  for (const Layer &L : S->layers)
+    per_step += (uint64_t)L.out_size *
+                ((S->mode == FHE_LIF_TWO_PBS && L.type != FHE_LAYER_POISSON) ? 2u : 1u);
+  return per_step * S->desc.T;
 }
 
 extern "C" uint32_t fhe_snn_iterations(const fhe_snn *S) { return S ? snn_iterations(S) : 0u; }
@@ -217,17 +254,42 @@ extern "C" int fhe_snn_profile(const fhe_snn *S, double *br_ms, uint64_t *br_lau
   return FHE_OK;
 }
 
+// Bootstrap the ciphertexts [lo, hi) of `in` with `lut` into `out` (table
+// stride `stride`), bracketed by profiling slot `slot` of iteration tau.
+static int snn_bootstrap(fhe_snn *S, uint32_t tau, uint32_t slot, const uint32_t *in, size_t lo,
+                         size_t hi, const fhe_lut *lut, uint32_t *out, size_t stride,
+                         cudaStream_t st) {
+  const uint32_t W = S->K->P.n + 1u;
+  if (hi <= lo) return FHE_OK;
+  const size_t e = 2u * tau + slot;
+  if (S->profile) {
+    S->K->prof_ev0 = S->ev[2u * e];
+    S->K->prof_ev1 = S->ev[2u * e + 1u];
+  }
+  const int rc = fhe::pbs_run(S->K, in + lo * W, hi - lo, lut, out + lo * W, stride,
+                              S->desc.variant, st);
+  if (S->profile) {
+    S->ev_count[e] = S->K->prof_count;
+    S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
+  }
+  return rc;
+}
+
 // Enqueue iteration tau for `ni` images: every layer l with t = tau - l in
-// [0, T) advances one step; their bootstraps share one launch.
+// [0, T) advances one step; their bootstraps share one launch (two in the
+// two-bootstrap mode: Fire over all active layers, Reset over the LIF ones).
 static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
   const fhe::Params &P = S->K->P;
   const uint32_t W = P.n + 1u;
-  const uint32_t half_p = P.delta() * (P.p() / 2u);  // (p/2) * Delta
+  const uint32_t delta = P.delta();
+  const uint32_t half_p = delta * (P.p() / 2u);  // (p/2) * Delta
   const uint32_t T = S->desc.T, nl = (uint32_t)S->layers.size();
   const uint32_t lo = (tau >= T) ? tau - T + 1u : 0u;
   const uint32_t hi = (tau < nl - 1u) ? tau : nl - 1u;
   const size_t all = ni * S->neurons;
+  const bool two = (S->mode == FHE_LIF_TWO_PBS);
   uint32_t *spk = S->d_out, *mem = S->d_out + all * W;
+  uint32_t *fire_in = two ? S->d_Hf : S->d_H;
   // segment offsets of the layers (ciphertexts) for this batch size
   std::vector<size_t> off(nl + 1u, 0);
   for (uint32_t l = 0; l < nl; ++l) off[l + 1] = off[l] + ni * S->layers[l].out_size;
@@ -237,6 +299,7 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
   for (uint32_t l = lo; l <= hi; ++l) {
     Layer &L = S->layers[l];
     const uint32_t t = tau - l;
+    if (L.type == FHE_LAYER_POISSON) continue;  // no WeightSum: compares pixels
     const bool static_first = (l == 0 && S->desc.static_input);
     if (static_first && t > 0) continue;  // the conv of the pixels is time-invariant
     const uint32_t *x = (l == 0)
@@ -249,25 +312,41 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
                           L.pad, NULL, x, ni, L.d_I, st);
     if (rc) return rc;
   }
-  // 2. H = V + I, centred by +p/2 (V = 0 at the layer's first step)
+  // 2. bootstrap inputs.  LIF: H = V + I (V = 0 at the layer's first step),
+  //    centred by +p/2 (multi-value) or also H - V_th for the sign bootstrap
+  //    (two bootstraps).  Poisson: x - M_t + V_th - 1, centred (multi-value),
+  //    or x - M_t - 1 (two bootstraps).
   for (uint32_t l = lo; l <= hi; ++l) {
+    const Layer &L = S->layers[l];
     const uint32_t t = tau - l;
-    rc = fhe::lwe_add(P.n, S->layers[l].d_I, t ? mem + off[l] * W : NULL, half_p,
-                      ni * S->layers[l].out_size, S->d_H + off[l] * W, st);
+    const uint64_t cnt = ni * L.out_size;
+    if (L.type == FHE_LAYER_POISSON) {
+      const uint32_t cst = two ? (0u - delta) : ((uint32_t)(S->desc.v_th - 1) * delta + half_p);
+      rc = fhe::lwe_add_offsets(P.n, S->d_input, L.d_w + (size_t)t * L.in_size, L.in_size, 0u - delta,
+                                cst, cnt, fire_in + off[l] * W, st);
+      if (rc) return rc;
+      continue;
+    }
+    rc = fhe::lwe_add(P.n, L.d_I, t ? mem + off[l] * W : NULL, two ? 0u : half_p, cnt,
+                      S->d_H + off[l] * W, st);
+    if (!rc && two)
+      rc = fhe::lwe_add(P.n, S->d_H + off[l] * W, NULL, 0u - (uint32_t)S->desc.v_th * delta, cnt,
+                        S->d_Hf + off[l] * W, st);
     if (rc) return rc;
   }
-  // 3. one bootstrap launch for every active neuron: spikes and V in place
-  if (S->profile) {
-    S->K->prof_ev0 = S->ev[2u * tau];
-    S->K->prof_ev1 = S->ev[2u * tau + 1u];
+  // 3. bootstraps for every active neuron: spikes and V in place
+  if (!two) {
+    rc = snn_bootstrap(S, tau, 0u, S->d_H, off[lo], off[hi + 1], S->lut, spk, all * W, st);
+    if (rc) return rc;
+  } else {
+    rc = snn_bootstrap(S, tau, 0u, S->d_Hf, off[lo], off[hi + 1], S->lut_fire, spk, all * W, st);
+    if (!rc)  // 2 FHE-Fire = bootstrap_sign + 1
+      rc = fhe::lwe_add(P.n, spk + off[lo] * W, NULL, delta, off[hi + 1] - off[lo], spk + off[lo] * W, st);
+    const uint32_t lr = (S->layers[lo].type == FHE_LAYER_POISSON) ? lo + 1u : lo;
+    if (!rc && lr <= hi)
+      rc = snn_bootstrap(S, tau, 1u, S->d_H, off[lr], off[hi + 1], S->lut_reset, mem, all * W, st);
+    if (rc) return rc;
   }
-  rc = fhe::pbs_run(S->K, S->d_H + off[lo] * W, off[hi + 1] - off[lo], S->lut, spk + off[lo] * W,
-                    all * W, S->desc.variant, st);
-  if (S->profile) {
-    S->ev_count[tau] = S->K->prof_count;
-    S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
-  }
-  if (rc) return rc;
   // 4. spike-count scores of the last layer
   if (hi == nl - 1u) {
     const uint32_t t = tau - (nl - 1u);
@@ -285,7 +364,7 @@ static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
   fhe_snn::GraphSet set;
   set.execs.assign(iters, (cudaGraphExec_t)0);
   set.kernels.assign(iters, 0);
-  set.pbs_counts.assign(iters, 0);
+  set.pbs_counts.assign(2u * iters, 0);
   int rc = FHE_OK;
   for (uint32_t tau = 0; tau < iters && rc == FHE_OK; ++tau) {
     cudaGraph_t graph;
@@ -299,7 +378,8 @@ static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
     rc = snn_iteration(S, tau, ni, st);
     set.kernels[tau] = (int64_t)fhe::launches() - before;
     fhe::note_launches(-set.kernels[tau]);
-    if (S->profile) set.pbs_counts[tau] = S->ev_count[tau];
+    if (S->profile)
+      for (uint32_t k = 0; k < 2u; ++k) set.pbs_counts[2u * tau + k] = S->ev_count[2u * tau + k];
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (rc) { if (e == cudaSuccess) cudaGraphDestroy(graph); break; }
     if (e != cudaSuccess) { (void)cudaGetLastError(); rc = FHE_ECUDA; break; }
@@ -348,7 +428,8 @@ extern "C" int fhe_snn_step(fhe_snn *S, void *stream) {
     FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
     FHE_CUDA_TRY(cudaGraphLaunch(set.execs[tau], S->gs));
     fhe::note_launches(set.kernels[tau]);
-    if (S->profile) S->ev_count[tau] = set.pbs_counts[tau];
+    if (S->profile)
+      for (uint32_t k = 0; k < 2u; ++k) S->ev_count[2u * tau + k] = set.pbs_counts[2u * tau + k];
     FHE_CUDA_TRY(cudaEventRecord(S->join_out, S->gs));
     FHE_CUDA_TRY(cudaStreamWaitEvent(st, S->join_out, 0));
   } else {

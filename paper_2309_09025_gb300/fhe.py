@@ -24,7 +24,8 @@ VARIANT_EXACT = 0
 VARIANT_TC = 1
 VARIANT_FFT = 2
 KEY_LWE, KEY_GLWE, KEY_BSK, KEY_KSK = 0, 1, 2, 3
-LAYER_FC, LAYER_CONV = 0, 1
+LAYER_FC, LAYER_CONV, LAYER_POISSON = 0, 1, 2
+LIF_MULTI_VALUE, LIF_TWO_PBS = 0, 1
 SNN_PROFILE = 2
 
 # Every symbol the header declares (checked by the CPU test-suite).
@@ -74,7 +75,8 @@ class SnnDesc(ctypes.Structure):
                 ("v_th", ctypes.c_int32), ("leak_shift", ctypes.c_int32),
                 ("spike_scale", ctypes.c_int32), ("T", ctypes.c_uint32),
                 ("static_input", ctypes.c_int32), ("max_images", ctypes.c_uint32),
-                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("lif_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -326,11 +328,15 @@ class Snn:
         self._weights = []
         descs = (LayerDesc * len(net["layers"]))()
         for i, layer in enumerate(net["layers"]):
-            Wt = np.ascontiguousarray(np.asarray(layer["W"], np.int32))
+            Wt = np.ascontiguousarray(np.asarray(layer["M" if layer["type"] == "poisson" else "W"],
+                                                 np.int32))
             self._weights.append(Wt)
             d = descs[i]
             d.weights = Wt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-            if layer["type"] == "fc":
+            if layer["type"] == "poisson":
+                d.type = LAYER_POISSON
+                d.in_size = d.out_size = Wt.shape[1]
+            elif layer["type"] == "fc":
                 d.type = LAYER_FC
                 d.out_size, d.in_size = Wt.shape
             else:
@@ -341,7 +347,8 @@ class Snn:
         self.desc = SnnDesc(len(net["layers"]), descs, lif["v_th"], lif["leak_shift"],
                             lif["spike_scale"], net["T"], int(bool(net.get("static_input"))),
                             max_images, int(variant),
-                            int(bool(use_graph)) | (SNN_PROFILE if profile else 0))
+                            int(bool(use_graph)) | (SNN_PROFILE if profile else 0),
+                            LIF_TWO_PBS if net.get("lif_mode") == "two_pbs" else LIF_MULTI_VALUE)
         self._descs = descs
         h = ctypes.c_void_p()
         _check(lib().fhe_snn_create(keys.handle, ctypes.byref(self.desc), ctypes.byref(h)),

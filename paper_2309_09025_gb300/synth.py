@@ -40,6 +40,14 @@ LIF_DEFAULT = dict(v_th=8, leak_shift=1, spike_scale=1)
 # |I| <= p/2 - V_th on 64 calibration images (Thm 4.1's condition).
 CSNN_DIVISORS = (13, 15, 7)
 
+# Poisson-encoded comparison network (2.3, 5.1 Table Poisson): pixel
+# intensities quantised to POISSON_LEVELS levels, per-step thresholds M_t
+# uniform over the same levels (the paper draws M_t in [0, 255] against
+# normalised pixels; 16 levels keep x - M_t + V_th - 1 inside [-p/2, p/2) for
+# p = 64).  FC weight divisors chosen by oracle/calibrate_divisors.py.
+POISSON_LEVELS = 16
+POISSON_DIVISORS = (23, 7)
+
 
 def rng(seed):
     return np.random.Generator(np.random.PCG64(int(seed)))
@@ -123,6 +131,34 @@ def csnn_net(seed=2, T=4, divisors=CSNN_DIVISORS, raw=False):
     ]
     return {"layers": layers, "lif": dict(LIF_DEFAULT), "T": T, "static_input": True,
             "n_in": 28 * 28}
+
+
+def poisson_thresholds(seed, T, n, levels=POISSON_LEVELS):
+    """The server's public random matrices M_t of the Poisson encoder (2.3):
+    (T, n) int32, uniform in [0, levels)."""
+    return rng(seed).integers(0, levels, size=(T, n), dtype=np.int64).astype(np.int32)
+
+
+def poisson_fc_net(seed=7, T=20, levels=POISSON_LEVELS, divisors=POISSON_DIVISORS, raw=False,
+                   hidden=160, lif_mode="multi"):
+    """The Poisson-encoded fully connected SNN of the paper's comparison
+    (5.1, Table Poisson): Poisson encoder of the 784 pixels (one comparison
+    bootstrap per pixel and step) -> FC 784->hidden LIF -> FC hidden->10 LIF,
+    spike-count scores, T steps (the paper's T_1 is 20..100).  Pixels are
+    encrypted once (static input, quantised to `levels` levels)."""
+    g = rng(seed)
+    W1 = g.integers(-15, 16, size=(hidden, 784), dtype=np.int64)
+    W2 = g.integers(-15, 16, size=(10, hidden), dtype=np.int64)
+    if not raw:
+        W1 = _divide_round_away(W1, divisors[0])
+        W2 = _divide_round_away(W2, divisors[1])
+    layers = [
+        {"type": "poisson", "M": poisson_thresholds(seed + 1, T, 784, levels)},
+        {"type": "fc", "W": np.asarray(W1, np.int32)},
+        {"type": "fc", "W": np.asarray(W2, np.int32)},
+    ]
+    return {"layers": layers, "lif": dict(LIF_DEFAULT), "T": T, "static_input": True,
+            "n_in": 28 * 28, "levels": levels, "lif_mode": lif_mode}
 
 
 def paper_csnn_net(seed=6, T=2, wmax=3):
