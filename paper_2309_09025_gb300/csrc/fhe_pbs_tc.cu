@@ -58,10 +58,16 @@ constexpr int kBN = 256;          // output coefficients per block (MMA N)
 constexpr int kKB = 64;           // K elements per A tile
 constexpr int kATile = kBh * kKB * 2;   // 16 KB: one CTA's 128 rows x 64 K
 constexpr uint32_t kAStages = 9;  // A-operand pipeline depth (9 x 16 KB)
+// Accumulator staging of the digit phase: six buffers of 32 KB over the (then
+// idle) A and B stages.
+constexpr uint32_t kGBuf = 6;
 // One B window: the 128 columns of a CTA over K = 1024 of a Hankel strip,
 // (128 + 1024) / 8 core matrices of 128 bytes.
-constexpr uint32_t kBWin = (128u + 1024u) / 8u * 128u;
-constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
+constexpr uint32_t kBK = 1024;
+constexpr uint32_t kBWin = (128u + kBK) / 8u * 128u;
+constexpr int kThreads = 352;     // warp 0 A producer, warp 1 MMA, warps 2-9 epilogue,
+                                  // warp 10 B producer
+constexpr uint32_t kBWarp = 10;
 constexpr int kTmemCols = 512;
 
 // ---------------------------------------------------------------- PTX helpers
@@ -250,14 +256,14 @@ struct TcSmem {
   uint32_t a, b, bars, tmem_slot, total;
 };
 // A stages, then two B stages of two 128-column windows (one per limb of the
-// unit; each window covers K = 1024).  The B region also stages accumulators
-// during the digit phase (two buffers of 32 KB).
+// unit; each window covers K = 1024).  During the digit phase the A and B
+// regions stage accumulators instead (kGBuf buffers of 32 KB).
 __host__ __device__ inline TcSmem tc_smem() {
   TcSmem s;
   uint32_t o = 0;
   s.a = o; o += kAStages * kATile;
   s.b = o; o += 2u * 2u * kBWin;
-  s.bars = o; o += 48u * 8u;   // 3 x 9 + 11 mbarriers
+  s.bars = o; o += 48u * 8u;   // 3 x 9 + 6 + 3 + 6 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
@@ -279,7 +285,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                       int *status) {
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
   constexpr uint32_t KBLK = N / kKB;             // A tiles per digit row r
-  constexpr uint32_t KH = N / 1024u;             // B windows (K = 1024 each) per row
+  constexpr uint32_t KH = N / kBK;               // B windows per digit row
+  constexpr uint32_t KT = kBK / kKB;             // A tiles per B window
   constexpr uint32_t TILE_H = kATile / 2;        // fp16 elements of one A tile
   constexpr uint32_t G = 4096u / N;              // ciphertexts per staged group (32 KB)
   constexpr uint32_t NGROUP = 64u / G;
@@ -291,7 +298,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t *a_full = bars, *a_empty = bars + kAStages, *a_peer = bars + 2 * kAStages;
   uint64_t *b_full = bars + 3 * kAStages, *b_empty = b_full + 2, *b_peer = b_full + 4;
   uint64_t *t_full = b_full + 6, *t_empty = b_full + 7, *done = b_full + 8;
-  uint64_t *g_full = b_full + 9;  // two staging buffers of the digit phase
+  uint64_t *g_full = b_full + 9;  // staging buffers of the digit phase
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
   __shared__ uint32_t s_abar[64];  // a~_i of the 64 ciphertexts whose digits this CTA makes
@@ -327,8 +334,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); mbar_init(&b_peer[s], 1);
-      mbar_init(&g_full[s], 1);
     }
+    for (uint32_t s = 0; s < kGBuf; ++s) mbar_init(&g_full[s], 1);
     mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -369,7 +376,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   for (uint32_t i = 0; i < n; ++i) {
     // ---- digits of X^{a~_i} ACC - ACC for this CTA's 64 ciphertexts.
     // Groups of G ciphertexts (both polynomials, 32 KB) are staged in shared
-    // memory by bulk copies, double buffered.  One warp per chunk of 256
+    // memory by bulk copies, kGBuf groups in flight.  One warp per chunk of 256
     // coefficients of one polynomial; lane L owns c = c_base + 32k + L, so
     // shared-memory reads are conflict free and global stores coalesced.
     if (tid < 64u) {
@@ -379,79 +386,105 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
     }
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (uint32_t g = 0; g < 2u; ++g) {
-        mbar_expect_tx(&g_full[(g_it + g) & 1u], 32768u);
-        bulk_g2s(sB + ((g_it + g) & 1u) * 32768u, acc + (uint64_t)(row0 + g * G) * 2u * N, 32768u,
-                 &g_full[(g_it + g) & 1u]);
+      for (uint32_t g = 0; g < kGBuf && g < NGROUP; ++g) {
+        const uint32_t bf = (g_it + g) % kGBuf;
+        mbar_expect_tx(&g_full[bf], 32768u);
+        bulk_g2s(smem + bf * 32768u, acc + (uint64_t)(row0 + g * G) * 2u * N, 32768u, &g_full[bf]);
       }
     }
     __syncthreads();
     for (uint32_t g = 0; g < NGROUP; ++g, ++g_it) {
-      const uint32_t buf = g_it & 1u;
-      const bool got = wait_bounded(&g_full[buf], (g_it >> 1) & 1u, &s_abort);
-      const uint32_t *sacc = reinterpret_cast<const uint32_t *>(sB + buf * 32768u);
-      constexpr uint32_t CH = G * 2u * (N / 256u);  // = 32 chunks of 256
-      for (uint32_t chunk = warp; got && chunk < CH; chunk += kThreads / 32u) {
-        const uint32_t cb = chunk % (N / 256u), j = (chunk / (N / 256u)) & 1u;
-        const uint32_t gi = chunk / (2u * (N / 256u));
+      const uint32_t buf = g_it % kGBuf;
+      const bool got = wait_bounded(&g_full[buf], (g_it / kGBuf) & 1u, &s_abort);
+      const uint32_t *sacc = reinterpret_cast<const uint32_t *>(smem + buf * 32768u);
+      // Items (ciphertext gi, polynomial j, block of 128 coefficients); lane L
+      // owns the 4 consecutive coefficients c0 = 128 cb + 4L .. +3.  Their
+      // reversed indices t' = N-1-c form one aligned 8-byte run of a
+      // core-matrix row, so each gadget level is a single 8-byte store.
+      constexpr uint32_t NB = N / 128u;
+      constexpr uint32_t ITEMS = G * 2u * NB;  // = 64
+      for (uint32_t item = warp; got && item < ITEMS; item += kThreads / 32u) {
+        const uint32_t cb = item % NB, j = (item / NB) & 1u, gi = item / (2u * NB);
         const uint32_t bl = g * G + gi;             // 0..63
         const uint32_t bm = 64u * pj + bl;          // MMA row within this half
         const uint32_t a = s_abar[bl];
         const uint32_t *Pj = sacc + (gi * 2u + j) * N;
-        uint32_t xr[8];
+        const uint32_t c0 = cb * 128u + 4u * lane;
+        const uint4 me = *reinterpret_cast<const uint4 *>(Pj + c0);
+        // X^{a} P at c0..c0+3 reads P at s = c - a (mod 2N), negated where
+        // s >= N.  Aligned runs of 4 never straddle N, so the two aligned
+        // runs around s0 give all four values with one sign each.
+        const uint32_t s0 = (c0 + 2u * N - a) & (2u * N - 1u);
+        const uint32_t dl = s0 & 3u;                 // the same for every lane
+        const uint32_t sa = s0 - dl, sb = (sa + 4u) & (2u * N - 1u);
+        const uint4 ra = *reinterpret_cast<const uint4 *>(Pj + (sa & (N - 1u)));
+        const uint4 rb = *reinterpret_cast<const uint4 *>(Pj + (sb & (N - 1u)));
+        const uint32_t ma = (sa >= N) ? ~0u : 0u, mb = (sb >= N) ? ~0u : 0u;
+        const uint32_t w[8] = {(ra.x ^ ma) - ma, (ra.y ^ ma) - ma, (ra.z ^ ma) - ma, (ra.w ^ ma) - ma,
+                               (rb.x ^ mb) - mb, (rb.y ^ mb) - mb, (rb.z ^ mb) - mb, (rb.w ^ mb) - mb};
+        const uint32_t mev[4] = {me.x, me.y, me.z, me.w};
+        uint32_t xr[4];
 #pragma unroll
-        for (uint32_t k = 0; k < 8u; ++k) {
-          const uint32_t c = cb * 256u + 32u * k + lane;
-          const uint32_t s = (c + 2u * N - a) & (2u * N - 1u);
-          const uint32_t rot = (s < N) ? Pj[s] : (0u - Pj[s - N]);
-          xr[k] = rot - Pj[c];
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < 8u; ++k)
+        for (uint32_t k = 0; k < 4u; ++k) {
+          const uint32_t rot = (dl == 0u) ? w[k] : (dl == 1u) ? w[k + 1] : (dl == 2u) ? w[k + 2] : w[k + 3];
+          xr[k] = rot - mev[k];
           xr[k] = (total_bits >= 32u)
                       ? xr[k]
                       : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
+        }
+        const uint32_t tpb = N - 4u - c0;  // smallest reversed index of the run
+        const uint32_t in_tile = (bm / 8u) * 512u + ((tpb % 64u) / 8u) * 64u + (bm % 8u) * 8u + (tpb % 8u);
+        __half *dst0 = dig_h + (uint64_t)(tpb / 64u) * TILE_H + in_tile;
         // least significant level first (carries propagate upwards)
         for (int lam = (int)l - 1; lam >= 0; --lam) {
           const uint32_t r = j * l + (uint32_t)lam;
+          uint32_t hv[4], hh2[4];
 #pragma unroll
-          for (uint32_t k = 0; k < 8u; ++k) {
+          for (uint32_t k = 0; k < 4u; ++k) {
             const uint32_t d = xr[k] & Bmask;
             xr[k] >>= P.log2_bg;
             int32_t sd = (int32_t)d;
             if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
-            const uint32_t tp = N - 1u - (cb * 256u + 32u * k + lane);  // reversed index t'
-            const uint32_t in_tile = (bm / 8u) * 512u + ((tp % 64u) / 8u) * 64u + (bm % 8u) * 8u + (tp % 8u);
             if (sub_shift == 0u) {
-              dig_h[(uint64_t)(r * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(sd);
+              hv[k] = __half_as_ushort(__int2half_rn(sd));
+              hh2[k] = 0u;
             } else {
               const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
               int32_t lo = (int32_t)((uint32_t)sd & sm);
               if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
               const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
-              dig_h[(uint64_t)(r * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(lo);
-              dig_h[(uint64_t)((R + r) * KBLK + tp / 64u) * TILE_H + in_tile] = __int2half_rn(hi);
+              hv[k] = __half_as_ushort(__int2half_rn(lo));
+              hh2[k] = __half_as_ushort(__int2half_rn(hi));
             }
           }
+          // position tpb + m holds the digit of c0 + 3 - m
+          *reinterpret_cast<uint2 *>(dst0 + (uint64_t)r * KBLK * TILE_H) =
+              make_uint2(hv[3] | (hv[2] << 16), hv[1] | (hv[0] << 16));
+          if (sub_shift != 0u)
+            *reinterpret_cast<uint2 *>(dst0 + (uint64_t)(R + r) * KBLK * TILE_H) =
+                make_uint2(hh2[3] | (hh2[2] << 16), hh2[1] | (hh2[0] << 16));
         }
       }
       __syncthreads();  // buffer `buf` is free again
-      if (tid == 0 && g + 2u < NGROUP && !s_abort) {
+      if (tid == 0 && g + kGBuf < NGROUP && !s_abort) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&g_full[buf], 32768u);
-        bulk_g2s(sB + buf * 32768u, acc + (uint64_t)(row0 + (g + 2u) * G) * 2u * N, 32768u, &g_full[buf]);
+        bulk_g2s(smem + buf * 32768u, acc + (uint64_t)(row0 + (g + kGBuf) * G) * 2u * N, 32768u,
+                 &g_full[buf]);
       }
     }
-    // This CTA multicasts exactly the digit rows it just wrote; a CTA-wide
-    // barrier orders them (and the staging buffers' last reads) before its
-    // producer's bulk copies.
+    // This CTA multicasts exactly the digit rows it just wrote; the fence and
+    // barrier order them (and the staging buffers' last reads) before the
+    // bulk copies.  The barrier is cluster-wide because the partner CTA
+    // multicasts into this CTA's A stages, which staged accumulators until now.
     asm volatile("fence.proxy.async;" ::: "memory");
-    __syncthreads();
+    cluster_sync_all();
 
     // ---- external product units (block, limb pair, chunk) of output
     // polynomial pj: each A tile feeds both limbs of the pair (accumulators
     // in TMEM columns 0..255 and 256..511).
-    if (warp == 0) {
+    if (warp == 0 || warp == kBWarp) {
+      // producers: warp 0 streams the digit tiles, warp kBWarp the key windows
       if (lane == 0) {
         for (uint32_t blk = 0; blk < nblk; ++blk) {
           const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
@@ -460,24 +493,27 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t r = ch * chunk_r + rr;
-                  const uint32_t bs = b_it & 1u;
-                  if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
-                  if (!s_abort) {
-                    mbar_expect_tx(&b_full[bs], 2u * kBWin);
-                    for (uint32_t z = 0; z < 2u; ++z) {
-                      const __half *src = strips +
-                                          ((((uint64_t)i * R + r % R) * 2u + pj) * 4u + 2u * lp + z) * strip_halves +
-                                          (uint64_t)((c0 + 1024u * kh) / 8u) * 64u;
-                      bulk_g2s(sB + (bs * 2u + z) * kBWin, src, kBWin, &b_full[bs]);
+                  if (warp == kBWarp) {
+                    const uint32_t bs = b_it & 1u;
+                    if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
+                    if (!s_abort) {
+                      mbar_expect_tx(&b_full[bs], 2u * kBWin);
+                      for (uint32_t z = 0; z < 2u; ++z) {
+                        const __half *src = strips +
+                                            ((((uint64_t)i * R + r % R) * 2u + pj) * 4u + 2u * lp + z) * strip_halves +
+                                            (uint64_t)((c0 + kBK * kh) / 8u) * 64u;
+                        bulk_g2s(sB + (bs * 2u + z) * kBWin, src, kBWin, &b_full[bs]);
+                      }
                     }
+                    ++b_it;
+                    continue;
                   }
-                  ++b_it;
-                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                  for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     if (a_it >= kAStages)
                       wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
                     if (!s_abort) {
-                      const __half *src = dig_h + (uint64_t)(r * KBLK + 16u * kh + kb) * TILE_H + pj * (TILE_H / 2u);
+                      const __half *src = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H + pj * (TILE_H / 2u);
                       mbar_expect_tx(&a_full[as], kATile);
                       bulk_g2s_multicast(sA + as * kATile + pj * (kATile / 2), src, kATile / 2,
                                          &a_full[as], a_mask);
@@ -502,7 +538,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                   wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort);
                   wait_bounded(&b_peer[bs], (b_it >> 1) & 1u, &s_abort);
                   const uint32_t bbase = smem_u32(sB + bs * 2u * kBWin);
-                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                  for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
                     wait_bounded(&a_peer[as], (a_it / kAStages) & 1u, &s_abort);
@@ -541,7 +577,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                   if (wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort))
                     mbar_arrive_remote(bs ? bp1 : bp0);
                   ++b_it;
-                  for (uint32_t kb = 0; kb < 16u; ++kb) {
+                  for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     if (wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort))
                       mbar_arrive_remote(cluster_addr(&a_peer[as], lead));
@@ -550,7 +586,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                 }
       }
       __syncwarp();
-    } else {
+    } else if (warp >= 2u && warp < 10u) {
       // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (ciphertexts) and
       // columns 128 ((w - 2) / 4) .. +128 of both 256-column accumulators
       const uint32_t quarter = warp % 4u, half = (warp - 2u) / 4u;
