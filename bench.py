@@ -174,7 +174,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": workload_name(P, 4, 1) + " (CPU oracle sample)"},
+        "config": {"workload": workload_name(P, 4, args.images), "images_per_step": args.images,
+                   "sample": "each step times a bounded sample of this workload (%d bootstraps)"
+                             % n_pbs},
         "ms_per_prediction": 1e3 * per_image / value,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -201,7 +203,8 @@ def run_ours(args):
     T = 4
     B = args.images
     net = synth.csnn_net(T=T)
-    keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, B * 1152))
+    # workspace: one bootstrap launch holds every layer's neurons of a batch
+    keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, -(-B * 1290 // 256) * 256))
     images = synth.stroke_images(5 + rank, B)
     ct = fhe.encrypt(keys, images.reshape(-1), seed=11 + rank).view(B, 28 * 28, P["n"] + 1)
     variant = fhe.VARIANT_TC if args.variant == "tc" else fhe.VARIANT_EXACT
@@ -216,14 +219,22 @@ def run_ours(args):
             probe.free()
         except fhe.FheError:
             pass
-    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=True, profile=True)
+    streamed = args.schedule == "stream"
+    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=not streamed, profile=True)
     per_image = snn.pbs_per_image()
-    scores = torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda")
+    # two score buffers: a streamed batch's scores land during the next push
+    scores = [torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda") for _ in range(2)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
-        snn.infer(ct, B, scores)
+    def one_step(k):
+        if streamed:
+            snn.stream_push(ct, B, scores[k % 2])
+        else:
+            snn.infer(ct, B, scores[0])
+
+    for k in range(args.warmup):  # streamed: fills the pipeline
+        one_step(k)
     torch.cuda.synchronize()
 
     def barrier():
@@ -237,22 +248,29 @@ def run_ours(args):
     barrier()
     launches0 = fhe.kernel_launches()
     step_ms, br_ms, br_launches, br_cts = [], 0.0, 0, 0
-    for _ in range(args.steps):
+    prof0 = snn.profile() if streamed else (0.0, 0, 0)
+    for k in range(args.steps):
         flush.zero_()  # L2 flush (256 MiB > 129 MB L2), outside the timed events
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        snn.infer(ct, B, scores)
+        one_step(args.warmup + k)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        ms, nl, nc = snn.profile()
-        br_ms += ms
-        br_launches += nl
-        br_cts += nc
+        if not streamed:
+            ms, nl, nc = snn.profile()
+            br_ms += ms
+            br_launches += nl
+            br_cts += nc
     barrier()
     launches = fhe.kernel_launches() - launches0
     clk = clocks.stop()
+    if streamed:
+        ms, nl, nc = snn.profile()
+        br_ms, br_launches, br_cts = ms - prof0[0], nl - prof0[1], nc - prof0[2]
+        snn.stream_flush()  # completes the last batch, after the timed region
+        torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), world, "cuda")
     value = job_rate(per_image * B * args.steps, world, total_ms)
 
@@ -261,21 +279,32 @@ def run_ours(args):
     if not args.no_e2e:
         h_in = torch.empty(ct.shape, dtype=torch.int32, pin_memory=True)
         h_in.copy_(ct.cpu())
-        h_out = torch.empty(scores.shape, dtype=torch.int32, pin_memory=True)
-        snn.infer(h_in, B, h_out, on_host=True)  # warm the host path
+        h_out = [torch.empty(scores[0].shape, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+
+        def host_step(k):
+            if streamed:
+                snn.stream_push(h_in, B, h_out[k % 2], on_host=True)
+                torch.cuda.synchronize()  # the previous batch's scores are on the host now
+            else:
+                snn.infer(h_in, B, h_out[0], on_host=True)
+
+        for k in range(2 if streamed else 1):  # warm the host path (streamed: fill)
+            host_step(k)
         barrier()
         e2e_ms = []
-        for _ in range(args.e2e_steps):
+        for k in range(args.e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            snn.infer(h_in, B, h_out, on_host=True)
+            host_step(k)
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        if streamed:
+            snn.stream_flush()
         barrier()
         e2e_total = max_over_ranks(sum(e2e_ms), world, "cuda")
         e2e = {"value": job_rate(per_image * B * args.e2e_steps, world, e2e_total), "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel() * 4),
-               "d2h_bytes_per_step": int(h_out.numel() * 4)}
+               "d2h_bytes_per_step": int(h_out[0].numel() * 4)}
 
     if rank != 0:
         return
@@ -313,8 +342,13 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_name(P, T, B), "images_per_step": B,
                    "variant": "tc" if variant == fhe.VARIANT_TC else "exact",
-                   "schedule": "layer-skewed, one bootstrap launch per step, "
-                               "CUDA graph per step",
+                   "schedule": ("streamed: each timed step starts one batch and, in the same "
+                                "bootstrap launches, finishes the batch before it (pipeline "
+                                "filled by the warm-up steps, drained after the timed region); "
+                                "one bootstrap launch per layer-skewed iteration")
+                               if streamed else
+                               "one batch per step: layer-skewed, one bootstrap launch per "
+                               "iteration, CUDA graph per iteration",
                    "l2": "256 MiB buffer written before every timed step",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
         "ms_per_prediction": total_ms / args.steps / B,
@@ -338,6 +372,8 @@ def main():
     # two waves of the 36 co-resident 4-CTA clusters
     ap.add_argument("--images", type=int, default=7)
     ap.add_argument("--variant", default="auto", choices=["auto", "exact", "tc"])
+    ap.add_argument("--schedule", default="stream", choices=["stream", "batch"],
+                    help="stream: batches pipelined across steps; batch: one batch per step")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -308,6 +308,28 @@ int fhe_snn_end(fhe_snn *net, uint32_t *scores, int inputs_on_host, void *stream
 /* Number of steps of one inference (T + n_layers - 1). */
 uint32_t fhe_snn_iterations(const fhe_snn *net);
 
+/* Streamed inference of a sequence of batches (no counterpart in the paper:
+ * the serving form of the same computation).  Each push enqueues the T
+ * layer-skewed steps that start batch k and, in the same bootstrap launches,
+ * advance the layers of the batches still in flight, so that every launch
+ * holds every layer's neurons; each push runs exactly one batch's worth of
+ * bootstraps.  Batch k's encrypted scores [n_images][n_out][n+1] are written
+ * to `scores` (host memory if on_host, device otherwise; the input layout and
+ * on_host rule are those of fhe_snn_infer) by copies enqueued on `stream`
+ * once the batch completes, during a later push or the flush; host results
+ * are valid after `stream` synchronizes.  All batches of a stream have the
+ * same n_images (<= max_images).  The caller keeps `scores` valid until the
+ * batch completes.  fhe_snn_stream_flush runs the remaining steps so every
+ * pushed batch completes, synchronizes `stream` when any destination is host
+ * memory (returning the device status), and ends the stream.  While a stream
+ * runs, fhe_snn_infer / fhe_snn_begin return FHE_EINVAL (and vice versa);
+ * fhe_snn_profile covers the launches since the stream's first push.
+ * Errors: FHE_EINVAL, FHE_ENOMEM (first push allocates the stream state),
+ * FHE_ECUDA, FHE_ETIMEOUT. */
+int fhe_snn_stream_push(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
+                        int on_host, void *stream);
+int fhe_snn_stream_flush(fhe_snn *net, void *stream);
+
 /* Optional: device spike ciphertexts of layer `layer` at the last step of
  * the last inference, copied to device buffer dst [n_images][size][n+1]. */
 int fhe_snn_layer_spikes(const fhe_snn *net, uint32_t layer, uint32_t *dst, void *stream);

@@ -45,6 +45,16 @@ inline bool params_supported(const Params &p) {
   return true;
 }
 
+// Profiling event around a launch: inside a stream capture it must become an
+// external event node of the graph; outside a capture a plain record.
+inline cudaError_t record_prof_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t q = cudaStreamIsCapturing(st, &cs);
+  if (q != cudaSuccess) return q;
+  return cudaEventRecordWithFlags(e, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                              : cudaEventRecordDefault);
+}
+
 // ---------------------------------------------------------------- randomness
 // Domains of the counter-based draws (one independent stream per purpose).
 enum Domain : uint32_t {

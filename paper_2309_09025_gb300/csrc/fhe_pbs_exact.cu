@@ -427,7 +427,7 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
     const uint32_t *in = ct_in + s0 * (P.n + 1u);
     int rc;
     const bool prof = (s0 == 0) && K->prof_ev0;
-    if (prof) { FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev0, st, cudaEventRecordExternal)); K->prof_count = cnt; }
+    if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
     switch (P.N) {
       case 256: rc = launch_br<256, 8>(K, in, cnt, la, K->d_big, st); break;
       case 512: rc = launch_br<512, 8>(K, in, cnt, la, K->d_big, st); break;
@@ -436,7 +436,7 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
       default: return FHE_EUNSUPPORTED;
     }
     if (rc) return rc;
-    if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
+    if (prof) FHE_CUDA_TRY(record_prof_event(K->prof_ev1, st));
     for (uint32_t j = 0; j < lut->L; ++j) {
       rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
                             ct_out + (size_t)j * table_stride + s0 * (P.n + 1u), st);

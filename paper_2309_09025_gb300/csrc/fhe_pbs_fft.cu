@@ -278,7 +278,7 @@ int pbs_fft(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
     const bool prof = (s0 == 0) && K->prof_ev0;
-    if (prof) { FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev0, st, cudaEventRecordExternal)); K->prof_count = cnt; }
+    if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
     if (P.N == 1024u) {
       FHE_CUDA_TRY(cudaFuncSetAttribute(k_blind_rotate_fft<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_blind_rotate_fft<1024><<<(unsigned)cnt, kFftThreads, smem, st>>>(
@@ -292,7 +292,7 @@ int pbs_fft(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut
     }
     note_launches(1);
     FHE_CUDA_TRY(cudaGetLastError());
-    if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
+    if (prof) FHE_CUDA_TRY(record_prof_event(K->prof_ev1, st));
     for (uint32_t j = 0; j < lut->L; ++j) {
       rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
                             ct_out + (size_t)j * table_stride + s0 * (P.n + 1u), st);

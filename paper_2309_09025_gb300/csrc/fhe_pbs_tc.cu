@@ -766,13 +766,13 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
     const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
     const bool prof = (s0 == 0) && K->prof_ev0;
-    if (prof) { FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev0, st, cudaEventRecordExternal)); K->prof_count = cnt; }
+    if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
     kern<<<tiles * kCluster, kThreads, S.total, st>>>(
         P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
         (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status);
     note_launches(1);
     FHE_CUDA_TRY(cudaGetLastError());
-    if (prof) FHE_CUDA_TRY(cudaEventRecordWithFlags(K->prof_ev1, st, cudaEventRecordExternal));
+    if (prof) FHE_CUDA_TRY(record_prof_event(K->prof_ev1, st));
     for (uint32_t j = 0; j < lut->L; ++j) {
       rc = key_switch_batch(K, K->d_big + (size_t)j * cnt * P.big_words(), cnt,
                             ct_out + (size_t)j * table_stride + s0 * (P.n + 1u), st);

@@ -38,6 +38,23 @@ struct Layer {
   uint32_t cin, h, w, cout, kh, kw, stride, pad;
   uint32_t *d_I;  // [max_images][out][n+1] (not used by a Poisson layer)
 };
+
+// Streamed inference: batch b lives in slot b % nslots while its layers are
+// in flight (T + layers - 1 iterations); every iteration gathers the active
+// (layer, batch) segments into one contiguous bootstrap launch.
+struct StreamState {
+  size_t ni = 0;            // images per batch of the running stream (0: idle)
+  uint32_t nslots = 0;
+  uint64_t pushed = 0;      // batches pushed since the stream started
+  uint64_t next_iter = 0;   // next iteration of the stream
+  std::vector<std::vector<uint32_t *>> spk, mem, I;  // [slot][layer]
+  std::vector<uint32_t *> in, scores, dst;           // [slot]
+  std::vector<int> dst_host;                         // [slot]
+  uint32_t *stage_H = nullptr, *stage_Hf = nullptr, *pout = nullptr;
+  std::vector<cudaEvent_t> ev;   // [launch][2]
+  std::vector<size_t> ev_count;  // ciphertexts of each bracketed launch
+  size_t ev_used = 0;
+};
 }  // namespace
 
 struct fhe_snn {
@@ -72,6 +89,9 @@ struct fhe_snn {
   cudaStream_t gs;
   cudaEvent_t join_in, join_out;
   size_t last_images;
+  // streamed inference state (allocated on the first push)
+  StreamState *stream;
+  bool prof_stream;    // the last inference activity was a stream
   // instrumentation: one event pair per bootstrap launch of an iteration
   bool profile;
   std::vector<cudaEvent_t> ev;   // [iterations][2 launches][2]
@@ -82,8 +102,24 @@ static uint32_t snn_iterations(const fhe_snn *S) {
   return S->desc.T + (uint32_t)S->layers.size() - 1u;
 }
 
+static void stream_release(StreamState *Z) {
+  if (!Z) return;
+  for (auto *v : {&Z->spk, &Z->mem, &Z->I})
+    for (auto &slot : *v)
+      for (auto p : slot) cudaFree(p);
+  for (auto p : Z->in) cudaFree(p);
+  for (auto p : Z->scores) cudaFree(p);
+  cudaFree(Z->stage_H);
+  cudaFree(Z->stage_Hf);
+  cudaFree(Z->pout);
+  for (auto e : Z->ev)
+    if (e) cudaEventDestroy(e);
+  delete Z;
+}
+
 static void snn_release(fhe_snn *S) {
   if (!S) return;
+  stream_release(S->stream);
   for (auto &kv : S->graphs)
     for (auto &g : kv.second.execs)
       if (g) cudaGraphExecDestroy(g);
@@ -240,6 +276,21 @@ extern "C" int fhe_snn_profile(const fhe_snn *S, double *br_ms, uint64_t *br_lau
   FHE_CUDA_TRY(cudaDeviceSynchronize());
   double ms = 0.0;
   uint64_t launches = 0, cts = 0;
+  if (S->prof_stream && S->stream) {
+    const StreamState &Z = *S->stream;
+    for (size_t e = 0; e < Z.ev_used; ++e) {
+      if (!Z.ev_count[e]) continue;
+      float t = 0.f;
+      FHE_CUDA_TRY(cudaEventElapsedTime(&t, Z.ev[2 * e], Z.ev[2 * e + 1]));
+      ms += t;
+      launches += 1;
+      cts += Z.ev_count[e];
+    }
+    *br_ms = ms;
+    *br_launches = launches;
+    *br_ciphertexts = cts;
+    return FHE_OK;
+  }
   for (size_t e = 0; e < S->ev_count.size(); ++e) {
     if (!S->ev_count[e]) continue;
     float t = 0.f;
@@ -399,6 +450,8 @@ static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
 extern "C" int fhe_snn_begin(fhe_snn *S, const uint32_t *ct_input, size_t ni, int inputs_on_host,
                              void *stream) {
   if (!S || !ct_input || ni == 0 || ni > S->desc.max_images) return FHE_EINVAL;
+  if (S->stream && S->stream->ni) return FHE_EINVAL;  // a stream is running
+  S->prof_stream = false;
   const uint32_t W = S->K->P.n + 1u;
   const size_t in_words = ni * (S->desc.static_input ? 1u : S->desc.T) * S->n_in * W;
   FHE_CUDA_TRY(cudaMemcpyAsync(S->d_input, ct_input, sizeof(uint32_t) * in_words,
@@ -476,5 +529,219 @@ extern "C" int fhe_snn_layer_spikes(const fhe_snn *S, uint32_t layer, uint32_t *
   const size_t words = S->last_images * S->layers[layer].out_size * W;
   FHE_CUDA_TRY(cudaMemcpyAsync(dst, S->d_out + off * W, sizeof(uint32_t) * words,
                                cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return FHE_OK;
+}
+
+// ---------------------------------------------------------------- streaming
+static int stream_alloc(fhe_snn *S) {
+  if (S->stream) return FHE_OK;
+  StreamState *Z = new StreamState();
+  const uint32_t T = S->desc.T, nl = (uint32_t)S->layers.size();
+  const uint32_t W = S->K->P.n + 1u;
+  const size_t mi = S->desc.max_images;
+  Z->nslots = 1u + (nl - 1u + T - 1u) / T;  // batches in flight at once
+  const size_t in_words = mi * (S->desc.static_input ? 1u : T) * S->n_in * W;
+  const size_t all = mi * S->neurons;
+  bool ok = true;
+  auto get = [&](uint32_t **p, size_t words) {
+    if (ok && cudaMalloc(p, sizeof(uint32_t) * words) != cudaSuccess) { *p = nullptr; ok = false; }
+  };
+  Z->spk.assign(Z->nslots, std::vector<uint32_t *>(nl, nullptr));
+  Z->mem = Z->spk;
+  Z->I = Z->spk;
+  Z->in.assign(Z->nslots, nullptr);
+  Z->scores.assign(Z->nslots, nullptr);
+  Z->dst.assign(Z->nslots, nullptr);
+  Z->dst_host.assign(Z->nslots, 0);
+  for (uint32_t sl = 0; sl < Z->nslots; ++sl) {
+    for (uint32_t l = 0; l < nl; ++l) {
+      const size_t words = mi * S->layers[l].out_size * W;
+      get(&Z->spk[sl][l], words);
+      if (S->layers[l].type != FHE_LAYER_POISSON) {
+        get(&Z->mem[sl][l], words);
+        get(&Z->I[sl][l], words);
+      }
+    }
+    get(&Z->in[sl], in_words);
+    get(&Z->scores[sl], mi * S->n_out * W);
+  }
+  get(&Z->stage_H, all * W);
+  if (S->mode == FHE_LIF_TWO_PBS) get(&Z->stage_Hf, all * W);
+  get(&Z->pout, 2u * all * W);
+  if (!ok) { stream_release(Z); return FHE_ENOMEM; }
+  S->stream = Z;
+  return FHE_OK;
+}
+
+static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi, const fhe_lut *lut,
+                            uint32_t *out, size_t stride, cudaStream_t st) {
+  if (hi <= lo) return FHE_OK;
+  StreamState &Z = *S->stream;
+  const uint32_t W = S->K->P.n + 1u;
+  if (S->profile) {
+    if (2u * Z.ev_used + 2u > Z.ev.size()) {
+      cudaEvent_t a, b;
+      FHE_CUDA_TRY(cudaEventCreate(&a));
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); (void)cudaGetLastError(); return FHE_ECUDA; }
+      Z.ev.push_back(a);
+      Z.ev.push_back(b);
+      Z.ev_count.push_back(0);
+    }
+    S->K->prof_ev0 = Z.ev[2u * Z.ev_used];
+    S->K->prof_ev1 = Z.ev[2u * Z.ev_used + 1u];
+  }
+  const int rc = fhe::pbs_run(S->K, in + lo * W, hi - lo, lut, out + lo * W, stride, S->desc.variant, st);
+  if (S->profile) {
+    Z.ev_count[Z.ev_used++] = S->K->prof_count;
+    S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
+  }
+  return rc;
+}
+
+// Iteration j of the stream: layer l runs batch b = (j - l) / T at time
+// t = (j - l) mod T for every pushed batch b (same recurrence as the
+// layer-skewed schedule of one inference).
+static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
+  StreamState &Z = *S->stream;
+  const fhe::Params &P = S->K->P;
+  const uint32_t W = P.n + 1u, delta = P.delta();
+  const uint32_t half_p = delta * (P.p() / 2u);
+  const uint32_t T = S->desc.T, nl = (uint32_t)S->layers.size();
+  const bool two = (S->mode == FHE_LIF_TWO_PBS);
+  const size_t ni = Z.ni, all = S->desc.max_images * S->neurons;
+  std::vector<int> on(nl, 0);
+  std::vector<uint32_t> slot(nl, 0), tt(nl, 0);
+  std::vector<size_t> off(nl + 1u, 0);
+  for (uint32_t l = 0; l < nl; ++l) {
+    if (j >= l) {
+      const uint64_t b = (j - l) / T;
+      if (b < Z.pushed) {
+        on[l] = 1;
+        slot[l] = (uint32_t)(b % Z.nslots);
+        tt[l] = (uint32_t)((j - l) % T);
+      }
+    }
+    off[l + 1] = off[l] + (on[l] ? ni * S->layers[l].out_size : 0);
+  }
+  if (off[nl] == 0) return FHE_OK;
+  int rc;
+  // 1. WeightSums of the active layers from the previous iteration's spikes
+  for (uint32_t l = 0; l < nl; ++l) {
+    if (!on[l]) continue;
+    Layer &L = S->layers[l];
+    const uint32_t sl = slot[l], t = tt[l];
+    if (L.type == FHE_LAYER_POISSON) continue;
+    if (l == 0 && S->desc.static_input && t > 0) continue;  // time-invariant conv
+    const uint32_t *x = (l == 0) ? Z.in[sl] + (S->desc.static_input ? 0 : (size_t)t * ni * S->n_in * W)
+                                 : Z.spk[sl][l - 1];
+    if (L.type == FHE_LAYER_FC)
+      rc = fhe_lwe_linear(P.n, P.log2_p, L.d_w, L.out_size, L.in_size, NULL, x, ni, Z.I[sl][l], st);
+    else
+      rc = fhe_lwe_conv2d(P.n, P.log2_p, L.d_w, L.cin, L.h, L.w, L.cout, L.kh, L.kw, L.stride, L.pad,
+                          NULL, x, ni, Z.I[sl][l], st);
+    if (rc) return rc;
+  }
+  // 2. bootstrap inputs, gathered contiguously in layer order
+  for (uint32_t l = 0; l < nl; ++l) {
+    if (!on[l]) continue;
+    const Layer &L = S->layers[l];
+    const uint32_t sl = slot[l], t = tt[l];
+    const uint64_t cnt = ni * L.out_size;
+    uint32_t *h = Z.stage_H + off[l] * W, *hf = two ? Z.stage_Hf + off[l] * W : nullptr;
+    if (L.type == FHE_LAYER_POISSON) {
+      const uint32_t cst = two ? (0u - delta) : ((uint32_t)(S->desc.v_th - 1) * delta + half_p);
+      rc = fhe::lwe_add_offsets(P.n, Z.in[sl], L.d_w + (size_t)t * L.in_size, L.in_size, 0u - delta, cst,
+                                cnt, two ? hf : h, st);
+      if (rc) return rc;
+      continue;
+    }
+    rc = fhe::lwe_add(P.n, Z.I[sl][l], t ? Z.mem[sl][l] : NULL, two ? 0u : half_p, cnt, h, st);
+    if (!rc && two) rc = fhe::lwe_add(P.n, h, NULL, 0u - (uint32_t)S->desc.v_th * delta, cnt, hf, st);
+    if (rc) return rc;
+  }
+  // 3. one launch for every active neuron (two in the two-bootstrap mode)
+  uint32_t *pout_v = Z.pout + all * W;
+  if (!two) {
+    rc = stream_bootstrap(S, Z.stage_H, 0, off[nl], S->lut, Z.pout, all * W, st);
+  } else {
+    rc = stream_bootstrap(S, Z.stage_Hf, 0, off[nl], S->lut_fire, Z.pout, all * W, st);
+    if (!rc) rc = fhe::lwe_add(P.n, Z.pout, NULL, delta, off[nl], Z.pout, st);
+    const size_t lr = (on[0] && S->layers[0].type == FHE_LAYER_POISSON) ? off[1] : 0;
+    if (!rc) rc = stream_bootstrap(S, Z.stage_H, lr, off[nl], S->lut_reset, pout_v, all * W, st);
+  }
+  if (rc) return rc;
+  // 4. spikes and membranes back to their batch slots
+  for (uint32_t l = 0; l < nl; ++l) {
+    if (!on[l]) continue;
+    const size_t bytes = sizeof(uint32_t) * ni * S->layers[l].out_size * W;
+    FHE_CUDA_TRY(cudaMemcpyAsync(Z.spk[slot[l]][l], Z.pout + off[l] * W, bytes, cudaMemcpyDeviceToDevice, st));
+    if (S->layers[l].type != FHE_LAYER_POISSON)
+      FHE_CUDA_TRY(cudaMemcpyAsync(Z.mem[slot[l]][l], pout_v + off[l] * W, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  // 5. spike-count scores; a batch is complete after the last layer's step T-1
+  const uint32_t lo = nl - 1u;
+  if (on[lo]) {
+    const uint32_t sl = slot[lo], t = tt[lo];
+    rc = fhe::lwe_add(P.n, Z.spk[sl][lo], t ? Z.scores[sl] : NULL, 0u, ni * S->n_out, Z.scores[sl], st);
+    if (rc) return rc;
+    if (t == T - 1u)
+      FHE_CUDA_TRY(cudaMemcpyAsync(Z.dst[sl], Z.scores[sl], sizeof(uint32_t) * ni * S->n_out * W,
+                                   Z.dst_host[sl] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  }
+  return FHE_OK;
+}
+
+extern "C" int fhe_snn_stream_push(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
+                                   int on_host, void *stream) {
+  if (!S || !ct_input || !scores || ni == 0 || ni > S->desc.max_images || S->cur_images)
+    return FHE_EINVAL;
+  int rc = stream_alloc(S);
+  if (rc) return rc;
+  StreamState &Z = *S->stream;
+  if (Z.ni == 0) {  // a new stream
+    Z.ni = ni;
+    Z.pushed = 0;
+    Z.next_iter = 0;
+    Z.ev_used = 0;
+    S->prof_stream = true;
+  } else if (ni != Z.ni) {
+    return FHE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t T = S->desc.T, W = S->K->P.n + 1u;
+  const uint64_t b = Z.pushed;
+  const uint32_t sl = (uint32_t)(b % Z.nslots);
+  const size_t in_words = ni * (S->desc.static_input ? 1u : T) * S->n_in * W;
+  FHE_CUDA_TRY(cudaMemcpyAsync(Z.in[sl], ct_input, sizeof(uint32_t) * in_words,
+                               on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  Z.dst[sl] = scores;
+  Z.dst_host[sl] = on_host;
+  Z.pushed = b + 1u;
+  for (uint64_t j = b * T; j < (b + 1u) * T; ++j) {
+    rc = stream_iteration(S, j, st);
+    if (rc) return rc;
+  }
+  Z.next_iter = (b + 1u) * T;
+  return FHE_OK;
+}
+
+extern "C" int fhe_snn_stream_flush(fhe_snn *S, void *stream) {
+  if (!S) return FHE_EINVAL;
+  if (!S->stream || !S->stream->ni) return FHE_OK;
+  StreamState &Z = *S->stream;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t end = Z.pushed * S->desc.T + S->layers.size() - 1u;
+  for (uint64_t j = Z.next_iter; j < end; ++j) {
+    const int rc = stream_iteration(S, j, st);
+    if (rc) { Z.ni = 0; return rc; }
+  }
+  Z.next_iter = end;
+  bool host = false;
+  for (uint32_t sl = 0; sl < Z.nslots; ++sl) host = host || Z.dst_host[sl];
+  Z.ni = 0;
+  if (host) {
+    FHE_CUDA_TRY(cudaStreamSynchronize(st));
+    return fhe_status(S->K, stream);
+  }
   return FHE_OK;
 }

@@ -37,6 +37,7 @@ EXPORTED = (
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
+    "fhe_snn_stream_push", "fhe_snn_stream_flush",
 )
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
@@ -123,6 +124,8 @@ def lib():
             "fhe_snn_iterations": (u32, [vp]),
             "fhe_selftest_timeout": (ctypes.c_int, [vp, u32, vp]),
             "fhe_fft_max_error": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+            "fhe_snn_stream_push": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
+            "fhe_snn_stream_flush": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -394,6 +397,24 @@ class Snn:
     def end(self, scores, stream=None):
         _check(lib().fhe_snn_end(self.handle, _ptr(scores), 0, _stream(stream)), "snn_end")
         return scores
+
+    def stream_push(self, ct_input, n_images, scores, on_host=False, stream=None):
+        """Start one batch of a streamed inference (fhe_snn_stream_push);
+        `scores` receives the batch's encrypted scores once it completes."""
+        if on_host:
+            def hp(x):
+                return (ctypes.c_void_p(x.data_ptr()) if hasattr(x, "data_ptr")
+                        else x.ctypes.data_as(ctypes.c_void_p))
+            pin, pout = hp(ct_input), hp(scores)
+        else:
+            pin, pout = _ptr(ct_input), _ptr(scores)
+        _check(lib().fhe_snn_stream_push(self.handle, pin, n_images, pout, int(bool(on_host)),
+                                         _stream(stream)), "snn_stream_push")
+        return scores
+
+    def stream_flush(self, stream=None):
+        """Complete every pushed batch and end the stream."""
+        _check(lib().fhe_snn_stream_flush(self.handle, _stream(stream)), "snn_stream_flush")
 
     def profile(self):
         """(blind-rotation ms, launches, ciphertexts) of the last inference."""
