@@ -40,7 +40,9 @@ SM_MAX_MHZ = 2070.0
 # from the ncu captures summarised in profiles/blind_rotate_*_p630.md (the key
 # layout is read once per launch from DRAM, so the figure does not scale with
 # the batch).  Set to None whenever the kernel changes until re-captured.
-TRAFFIC_BYTES = {"tc": None, "exact": 34.066688e6 + 16.64e3}
+# DRAM bytes (read + write) per launch of the dominant kernel, from ncu
+# captures of the same launches (summaries under profiles/).
+TRAFFIC_BYTES = {"tc": (1005565440 + 4784896 + 1006551552 + 2096128) / 2, "exact": 34.066688e6 + 16.64e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 
 
