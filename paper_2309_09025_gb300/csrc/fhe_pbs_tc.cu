@@ -19,7 +19,7 @@
 // Operands (SWIZZLE_NONE, K-major, 8x8 fp16 core matrices of 128 bytes), for
 // a CTA pair running tcgen05.mma.cta_group::2 with M = 256, N = 256, K = 16:
 //  - A = digits of 256 ciphertexts; each CTA holds its 128 rows in tiles of
-//    128 x 64 (LBO 128, SBO 1024).  Digits are written once per step to
+//    128 x 128 (LBO 128, SBO 2048).  Digits are written once per step to
 //    global memory and multicast by cp.async.bulk to the two CTAs (one per
 //    pair) that hold the same 128 rows; each of them sends the 64 rows it
 //    generated.
@@ -55,15 +55,18 @@ constexpr int kCluster = 4;       // two CTA pairs
 constexpr int kBt = 256;          // ciphertexts per cluster (MMA M of a CTA pair)
 constexpr int kBh = 128;          // ciphertexts per CTA (its half of M)
 constexpr int kBN = 256;          // output coefficients per block (MMA N)
-constexpr int kKB = 64;           // K elements per A tile
-constexpr int kATile = kBh * kKB * 2;   // 16 KB: one CTA's 128 rows x 64 K
-constexpr uint32_t kAStages = 9;  // A-operand pipeline depth (9 x 16 KB)
+constexpr int kKB = 128;          // K elements per A tile
+constexpr int kATile = kBh * kKB * 2;   // 32 KB: one CTA's 128 rows x 128 K
+// Byte distance between 8-row groups of an A tile (kKB / 8 core matrices).
+constexpr uint32_t kASBO = kKB / 8u * 128u;
+constexpr uint32_t kAStages = 5;  // A-operand pipeline depth (5 x 32 KB; large tiles keep the
+                                  // bulk copies efficient)
 // Accumulator staging of the digit phase: six buffers of 32 KB over the (then
 // idle) A and B stages.
 constexpr uint32_t kGBuf = 6;
 // One B window: the 128 columns of a CTA over K = 1024 of a Hankel strip,
 // (128 + 1024) / 8 core matrices of 128 bytes.
-constexpr uint32_t kBK = 1024;
+constexpr uint32_t kBK = 512;
 constexpr uint32_t kBWin = (128u + kBK) / 8u * 128u;
 constexpr int kThreads = 352;     // warp 0 A producer, warp 1 MMA, warps 2-9 epilogue,
                                   // warp 10 B producer
@@ -263,7 +266,7 @@ __host__ __device__ inline TcSmem tc_smem() {
   uint32_t o = 0;
   s.a = o; o += kAStages * kATile;
   s.b = o; o += 2u * 2u * kBWin;
-  s.bars = o; o += 48u * 8u;   // 3 x 9 + 6 + 3 + 6 mbarriers
+  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
@@ -433,11 +436,15 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                       : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
         }
         const uint32_t tpb = N - 4u - c0;  // smallest reversed index of the run
-        const uint32_t in_tile = (bm / 8u) * 512u + ((tpb % 64u) / 8u) * 64u + (bm % 8u) * 8u + (tpb % 8u);
-        __half *dst0 = dig_h + (uint64_t)(tpb / 64u) * TILE_H + in_tile;
+        const uint32_t in_tile = (bm / 8u) * (kKB * 8u) + ((tpb % kKB) / 8u) * 64u + (bm % 8u) * 8u + (tpb % 8u);
+        __half *dst0 = dig_h + (uint64_t)(tpb / kKB) * TILE_H + in_tile;
         // least significant level first (carries propagate upwards)
         for (int lam = (int)l - 1; lam >= 0; --lam) {
           const uint32_t r = j * l + (uint32_t)lam;
+          // A digit d with |d| < 512 is the fp16 number (1536 + d) - 1536,
+          // and the bits of 1536 + d are 0x6600 + d (1536 <= 1536 + d < 2048
+          // has an ulp of 1), so two digits become fp16 with one exact
+          // packed subtraction.
           uint32_t hv[4], hh2[4];
 #pragma unroll
           for (uint32_t k = 0; k < 4u; ++k) {
@@ -446,23 +453,29 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
             int32_t sd = (int32_t)d;
             if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
             if (sub_shift == 0u) {
-              hv[k] = __half_as_ushort(__int2half_rn(sd));
+              hv[k] = 0x6600u + (uint32_t)sd;
               hh2[k] = 0u;
             } else {
               const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
               int32_t lo = (int32_t)((uint32_t)sd & sm);
               if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
               const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
-              hv[k] = __half_as_ushort(__int2half_rn(lo));
-              hh2[k] = __half_as_ushort(__int2half_rn(hi));
+              hv[k] = 0x6600u + (uint32_t)lo;
+              hh2[k] = 0x6600u + (uint32_t)hi;
             }
           }
+          const __half2 off = __halves2half2(__ushort_as_half(0x6600u), __ushort_as_half(0x6600u));
+          auto pack = [&](uint32_t a, uint32_t b) {  // element a at the low half
+            const __half2 v = __hsub2(__halves2half2(__ushort_as_half((unsigned short)(a & 0xFFFFu)),
+                                                     __ushort_as_half((unsigned short)(b & 0xFFFFu))), off);
+            return *reinterpret_cast<const uint32_t *>(&v);
+          };
           // position tpb + m holds the digit of c0 + 3 - m
           *reinterpret_cast<uint2 *>(dst0 + (uint64_t)r * KBLK * TILE_H) =
-              make_uint2(hv[3] | (hv[2] << 16), hv[1] | (hv[0] << 16));
+              make_uint2(pack(hv[3], hv[2]), pack(hv[1], hv[0]));
           if (sub_shift != 0u)
             *reinterpret_cast<uint2 *>(dst0 + (uint64_t)(R + r) * KBLK * TILE_H) =
-                make_uint2(hh2[3] | (hh2[2] << 16), hh2[1] | (hh2[0] << 16));
+                make_uint2(pack(hh2[3], hh2[2]), pack(hh2[1], hh2[0]));
         }
       }
       __syncthreads();  // buffer `buf` is free again
@@ -546,11 +559,12 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!s_abort) {
                       const uint32_t abase = smem_u32(sA + as * kATile);
 #pragma unroll
-                      for (uint32_t s = 0; s < 4u; ++s) {
-                        const uint64_t ad = smem_desc(abase + s * 256u, 128u, 1024u);
+                      for (uint32_t s = 0; s < kKB / 16u; ++s) {
+                        const uint64_t ad = smem_desc(abase + s * 256u, 128u, kASBO);
 #pragma unroll
                         for (uint32_t z = 0; z < 2u; ++z) {
-                          const uint64_t bd = smem_desc(bbase + z * kBWin + (8u * kb + 2u * s) * 128u, 128u, 128u);
+                          const uint64_t bd = smem_desc(bbase + z * kBWin + ((kKB / 8u) * kb + 2u * s) * 128u,
+                                                        128u, 128u);
                           tc2_mma_f16(tmem + z * (uint32_t)kBN, ad, bd, idesc, accum);
                         }
                         accum = 1u;
@@ -712,6 +726,9 @@ static uint32_t tc_chunk_r(const Params &P) {
 
 static bool tc_supported(const Params &P) {
   const uint32_t s = tc_sub_shift(P);
+  // digits (or sub-digits) must stay below 512 in magnitude for the fp16
+  // conversion of the digit phase
+  if ((s ? (1u << (s - 1u)) : (1u << (P.log2_bg - 1u))) >= 512u) return false;
   // the high sub-digit must also fit: |hi| <= 2^(log2_bg - s - 1) + 1 <= 2^(s-1)
   if (s && (1u << (P.log2_bg - s - 1u)) > (1u << (s - 1u))) return false;
   return P.k == 1u && (P.N == 1024u || P.N == 2048u) && tc_chunk_r(P) >= 1u;
