@@ -400,82 +400,103 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
       const uint32_t buf = g_it % kGBuf;
       const bool got = wait_bounded(&g_full[buf], (g_it / kGBuf) & 1u, &s_abort);
       const uint32_t *sacc = reinterpret_cast<const uint32_t *>(smem + buf * 32768u);
-      // Items (ciphertext gi, polynomial j, block of 128 coefficients); lane L
-      // owns the 4 consecutive coefficients c0 = 128 cb + 4L .. +3.  Their
-      // reversed indices t' = N-1-c form one aligned 8-byte run of a
-      // core-matrix row, so each gadget level is a single 8-byte store.
-      constexpr uint32_t NB = N / 128u;
-      constexpr uint32_t ITEMS = G * 2u * NB;  // = 64
+      // Items (ciphertext gi, polynomial j, block of 256 coefficients); lane L
+      // owns two runs of 4 consecutive coefficients, c0 = 256 cb + 128 h + 4L
+      // (h = 0, 1), computed side by side.  The reversed indices t' = N-1-c
+      // of a run form one aligned 8-byte piece of a core-matrix row, so each
+      // gadget level is a single 8-byte store per run.
+      constexpr uint32_t NB = N / 256u;
+      constexpr uint32_t ITEMS = G * 2u * NB;  // = 32
       for (uint32_t item = warp; got && item < ITEMS; item += kThreads / 32u) {
         const uint32_t cb = item % NB, j = (item / NB) & 1u, gi = item / (2u * NB);
         const uint32_t bl = g * G + gi;             // 0..63
         const uint32_t bm = 64u * pj + bl;          // MMA row within this half
         const uint32_t a = s_abar[bl];
         const uint32_t *Pj = sacc + (gi * 2u + j) * N;
-        const uint32_t c0 = cb * 128u + 4u * lane;
-        const uint4 me = *reinterpret_cast<const uint4 *>(Pj + c0);
-        // X^{a} P at c0..c0+3 reads P at s = c - a (mod 2N), negated where
-        // s >= N.  Aligned runs of 4 never straddle N, so the two aligned
-        // runs around s0 give all four values with one sign each.
-        const uint32_t s0 = (c0 + 2u * N - a) & (2u * N - 1u);
-        const uint32_t dl = s0 & 3u;                 // the same for every lane
-        const uint32_t sa = s0 - dl, sb = (sa + 4u) & (2u * N - 1u);
-        const uint4 ra = *reinterpret_cast<const uint4 *>(Pj + (sa & (N - 1u)));
-        const uint4 rb = *reinterpret_cast<const uint4 *>(Pj + (sb & (N - 1u)));
-        const uint32_t ma = (sa >= N) ? ~0u : 0u, mb = (sb >= N) ? ~0u : 0u;
-        const uint32_t w[8] = {(ra.x ^ ma) - ma, (ra.y ^ ma) - ma, (ra.z ^ ma) - ma, (ra.w ^ ma) - ma,
-                               (rb.x ^ mb) - mb, (rb.y ^ mb) - mb, (rb.z ^ mb) - mb, (rb.w ^ mb) - mb};
-        const uint32_t mev[4] = {me.x, me.y, me.z, me.w};
-        uint32_t xr[4];
+        uint32_t xr[2][4];
+        __half *dst0[2];
 #pragma unroll
-        for (uint32_t k = 0; k < 4u; ++k) {
-          const uint32_t rot = (dl == 0u) ? w[k] : (dl == 1u) ? w[k + 1] : (dl == 2u) ? w[k + 2] : w[k + 3];
-          xr[k] = rot - mev[k];
-          xr[k] = (total_bits >= 32u)
-                      ? xr[k]
-                      : ((uint32_t)(xr[k] + (1u << (31u - total_bits))) >> (32u - total_bits));
-        }
-        const uint32_t tpb = N - 4u - c0;  // smallest reversed index of the run
-        const uint32_t in_tile = (bm / 8u) * (kKB * 8u) + ((tpb % kKB) / 8u) * 64u + (bm % 8u) * 8u + (tpb % 8u);
-        __half *dst0 = dig_h + (uint64_t)(tpb / kKB) * TILE_H + in_tile;
-        // least significant level first (carries propagate upwards)
-        for (int lam = (int)l - 1; lam >= 0; --lam) {
-          const uint32_t r = j * l + (uint32_t)lam;
-          // A digit d with |d| < 512 is the fp16 number (1536 + d) - 1536,
-          // and the bits of 1536 + d are 0x6600 + d (1536 <= 1536 + d < 2048
-          // has an ulp of 1), so two digits become fp16 with one exact
-          // packed subtraction.
-          uint32_t hv[4], hh2[4];
+        for (uint32_t h = 0; h < 2u; ++h) {
+          const uint32_t c0 = cb * 256u + 128u * h + 4u * lane;
+          const uint4 me = *reinterpret_cast<const uint4 *>(Pj + c0);
+          // X^{a} P at c0..c0+3 reads P at s = c - a (mod 2N), negated where
+          // s >= N.  Aligned runs of 4 never straddle N, so the two aligned
+          // runs around s0 give all four values with one sign each (applied
+          // as a multiplication by +-1).
+          const uint32_t s0 = (c0 + 2u * N - a) & (2u * N - 1u);
+          const uint32_t dl = s0 & 3u;               // the same for every lane
+          const uint32_t sa = s0 - dl, sb = (sa + 4u) & (2u * N - 1u);
+          const uint4 ra = *reinterpret_cast<const uint4 *>(Pj + (sa & (N - 1u)));
+          const uint4 rb = *reinterpret_cast<const uint4 *>(Pj + (sb & (N - 1u)));
+          const uint32_t ga = (sa >= N) ? 0xFFFFFFFFu : 1u, gb = (sb >= N) ? 0xFFFFFFFFu : 1u;
+          const uint32_t w[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+          const uint32_t mev[4] = {me.x, me.y, me.z, me.w};
+          uint32_t rot[4];
+          // dl is uniform across the warp: one branch, constant indices
+#define FHE_ROT(D)                                                               \
+  _Pragma("unroll") for (uint32_t k = 0; k < 4u; ++k)                            \
+      rot[k] = w[k + (D)] * ((k + (D)) < 4u ? ga : gb);
+          switch (dl) {
+            case 0u: FHE_ROT(0u) break;
+            case 1u: FHE_ROT(1u) break;
+            case 2u: FHE_ROT(2u) break;
+            default: FHE_ROT(3u) break;
+          }
+#undef FHE_ROT
 #pragma unroll
           for (uint32_t k = 0; k < 4u; ++k) {
-            const uint32_t d = xr[k] & Bmask;
-            xr[k] >>= P.log2_bg;
-            int32_t sd = (int32_t)d;
-            if (d >= Bhalf) { sd -= (int32_t)(Bmask + 1u); xr[k] += 1u; }
-            if (sub_shift == 0u) {
-              hv[k] = 0x6600u + (uint32_t)sd;
-              hh2[k] = 0u;
-            } else {
-              const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
-              int32_t lo = (int32_t)((uint32_t)sd & sm);
-              if ((uint32_t)lo >= sh) lo -= (int32_t)(sm + 1u);
-              const int32_t hi = (sd - lo) / (int32_t)(sm + 1u);  // exact division
-              hv[k] = 0x6600u + (uint32_t)lo;
-              hh2[k] = 0x6600u + (uint32_t)hi;
-            }
+            const uint32_t x = rot[k] - mev[k];
+            xr[h][k] = (total_bits >= 32u)
+                           ? x
+                           : ((uint32_t)(x + (1u << (31u - total_bits))) >> (32u - total_bits));
           }
-          const __half2 off = __halves2half2(__ushort_as_half(0x6600u), __ushort_as_half(0x6600u));
-          auto pack = [&](uint32_t a, uint32_t b) {  // element a at the low half
-            const __half2 v = __hsub2(__halves2half2(__ushort_as_half((unsigned short)(a & 0xFFFFu)),
-                                                     __ushort_as_half((unsigned short)(b & 0xFFFFu))), off);
-            return *reinterpret_cast<const uint32_t *>(&v);
-          };
-          // position tpb + m holds the digit of c0 + 3 - m
-          *reinterpret_cast<uint2 *>(dst0 + (uint64_t)r * KBLK * TILE_H) =
-              make_uint2(pack(hv[3], hv[2]), pack(hv[1], hv[0]));
-          if (sub_shift != 0u)
-            *reinterpret_cast<uint2 *>(dst0 + (uint64_t)(R + r) * KBLK * TILE_H) =
-                make_uint2(pack(hh2[3], hh2[2]), pack(hh2[1], hh2[0]));
+          const uint32_t tpb = N - 4u - c0;  // smallest reversed index of the run
+          const uint32_t in_tile = (bm / 8u) * (kKB * 8u) + ((tpb % kKB) / 8u) * 64u + (bm % 8u) * 8u + (tpb % 8u);
+          dst0[h] = dig_h + (uint64_t)(tpb / kKB) * TILE_H + in_tile;
+        }
+        // A digit d with |d| < 512 is the fp16 number (1536 + d) - 1536, and
+        // the bits of 1536 + d are 0x6600 + d (1536 <= 1536 + d < 2048 has an
+        // ulp of 1), so two digits become fp16 with one exact packed
+        // subtraction.
+        const __half2 off = __halves2half2(__ushort_as_half(0x6600u), __ushort_as_half(0x6600u));
+        auto pack = [&](uint32_t lo16, uint32_t hi16) {  // lo16 at the low half
+          const __half2 v = __hsub2(__halves2half2(__ushort_as_half((unsigned short)(lo16 & 0xFFFFu)),
+                                                   __ushort_as_half((unsigned short)(hi16 & 0xFFFFu))), off);
+          return *reinterpret_cast<const uint32_t *>(&v);
+        };
+        // least significant level first.  With v = u + B/2, the balanced
+        // digit is (v mod B) - B/2 and the carry-propagated rest is v >> beta
+        // (a digit d0 >= B/2 becomes d0 - B and carries 1).
+        const uint32_t bias = 0x6600u - Bhalf;  // fp16-bit offset minus B/2
+        for (int lam = (int)l - 1; lam >= 0; --lam) {
+          const uint32_t r = j * l + (uint32_t)lam;
+#pragma unroll
+          for (uint32_t h = 0; h < 2u; ++h) {
+            uint32_t hv[4], hh2[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4u; ++k) {
+              const uint32_t v = xr[h][k] + Bhalf;
+              xr[h][k] = v >> P.log2_bg;
+              if (sub_shift == 0u) {
+                hv[k] = (v & Bmask) + bias;
+                hh2[k] = 0u;
+              } else {
+                const int32_t sd = (int32_t)(v & Bmask) - (int32_t)Bhalf;
+                const uint32_t sm = (1u << sub_shift) - 1u, sh = 1u << (sub_shift - 1u);
+                const uint32_t vl = (uint32_t)sd + sh;           // same split for the sub-digits
+                const int32_t lo = (int32_t)(vl & sm) - (int32_t)sh;
+                const int32_t hi = (sd - lo) >> sub_shift;       // exact: sd - lo is a multiple
+                hv[k] = 0x6600u + (uint32_t)lo;
+                hh2[k] = 0x6600u + (uint32_t)hi;
+              }
+            }
+            // position tpb + m holds the digit of c0 + 3 - m
+            *reinterpret_cast<uint2 *>(dst0[h] + (uint64_t)r * KBLK * TILE_H) =
+                make_uint2(pack(hv[3], hv[2]), pack(hv[1], hv[0]));
+            if (sub_shift != 0u)
+              *reinterpret_cast<uint2 *>(dst0[h] + (uint64_t)(R + r) * KBLK * TILE_H) =
+                  make_uint2(pack(hh2[3], hh2[2]), pack(hh2[1], hh2[0]));
+          }
         }
       }
       __syncthreads();  // buffer `buf` is free again
