@@ -30,12 +30,14 @@ def main():
     build.build()
     P = dict(synth.PRESETS[args.params])
     p = 1 << P["log2_p"]
-    keys = fhe.keygen_from_seed(P, seed=args.seed)
+    batches = [int(b) for b in args.batches.split(",")]
+    # workspace for the largest batch, so that no batch is split into chunks
+    keys = fhe.keygen_from_seed(P, seed=args.seed, max_batch=max(16384, -(-max(batches) // 256) * 256))
     lut = fhe.lut_create(keys, synth.identity_plus_threshold_lut(p)[None])
     macs = P["n"] * (P["k"] + 1) ** 2 * P["l"] * P["N"] ** 2
     for variant in args.variants.split(","):
         v = {"exact": fhe.VARIANT_EXACT, "tc": fhe.VARIANT_TC, "fft": fhe.VARIANT_FFT}[variant]
-        for batch in [int(b) for b in args.batches.split(",")]:
+        for batch in batches:
             msgs = synth.uniform_messages(args.seed + batch, batch, p)
             ct = fhe.encrypt(keys, msgs, seed=1000 + batch)
             out = torch.empty((1, batch, P["n"] + 1), dtype=torch.int32, device="cuda")
