@@ -149,3 +149,20 @@ def test_two_pbs_requires_spike_value_two(fhe):
     with pytest.raises(fhe.FheError) as e:
         fhe.Snn(K, net, max_images=1)
     assert e.value.code == fhe.FHE_EINVAL
+
+
+def test_paper_csnn_small_ring_bit_exact(fhe, oracle_keys):
+    """The paper's CSNN topology (3.1; conv 1->10 8x8 s2 pad 1 -> 2x2 pooling
+    folded into FC 1440->160 (3.3) -> FC 160->10) on the small ring (N = 256,
+    p = 64), T = 2, scores bit-exact to the oracle through host buffers."""
+    P, K = gpu_keys(fhe, "P64", 9, log2_p=6)
+    _, OK = oracle_keys("P64", 9, log2_p=6)
+    net = synth.paper_csnn_net(T=2)
+    img = synth.stroke_images(3, 1).reshape(1, -1)
+    ct = O.encrypt(P, OK, img[0], 100)[None]
+    snn = make_snn(fhe, K, net, 1, "EXACT")
+    assert snn.pbs_per_image() == (1440 + 160 + 10) * 2
+    scores = np.zeros((1, 10, P["n"] + 1), np.uint32)
+    snn.infer(np.ascontiguousarray(ct), 1, scores, on_host=True)
+    ref = O.snn_encrypted(P, OK, net, ct[0], nthreads=NTHREADS)
+    assert np.array_equal(scores[0], ref["scores"])
