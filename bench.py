@@ -42,7 +42,7 @@ SM_MAX_MHZ = 2070.0
 # the batch).  Set to None whenever the kernel changes until re-captured.
 # DRAM bytes (read + write) per launch of the dominant kernel, from ncu
 # captures of the same launches (summaries under profiles/).
-TRAFFIC_BYTES = {"tc": (1005565440 + 4784896 + 1006551552 + 2096128) / 2, "exact": 34.066688e6 + 16.64e3}
+TRAFFIC_BYTES = {"tc": (1006311168 + 5379840 + 1005946368 + 2268416) / 2, "exact": 34.066688e6 + 16.64e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 
 
