@@ -235,14 +235,15 @@ def test_snn_csnn_topology_small_params_bit_exact(fhe, oracle_keys):
         assert np.array_equal(scores[i], ref["scores"])
 
 
-def test_tc_matches_exact_full_batch_p630(fhe, oracle_keys):
-    """Tensor-core blind rotation: every output of a multi-cluster P630 batch
-    (ragged against 128-ciphertext tiles) bit-identical to the CUDA-core path,
-    sampled outputs bit-identical to the oracle, for both table counts."""
-    P, K = gpu_keys(fhe, "P630", 3)
-    _, OK = oracle_keys("P630", 3)
+@pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 613)])
+def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
+    """Tensor-core blind rotation: every output of a multi-cluster batch
+    (ragged against 256-ciphertext cluster tiles) bit-identical to the
+    CUDA-core path, outputs at the tile edges bit-identical to the oracle, for
+    both table counts (P750: N = 2048 with split sub-digits)."""
+    P, K = gpu_keys(fhe, name, 3)
+    _, OK = oracle_keys(name, 3)
     p = 1 << P["log2_p"]
-    count = 389
     m = synth.uniform_messages(41, count, p)
     ct = fhe.encrypt(K, m, seed=7)
     for L in (1, 2):
@@ -251,9 +252,54 @@ def test_tc_matches_exact_full_batch_p630(fhe, oracle_keys):
         ref_gpu = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
         got = u32(pbs(fhe, K, ct, lut, "TC"))
         assert np.array_equal(got, ref_gpu)
-        idx = np.array([0, 127, 128, count - 1])
+        idx = np.array([0, 255, 256, count - 1])
         ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
         assert np.array_equal(got[:, idx], ref)
+    assert K.status() == fhe.FHE_OK
+
+
+def test_csnn_full_size_layer_chain_tc(fhe, oracle_keys):
+    """The bench's network at full size (P630, conv 1->8 5x5 s2 -> FC
+    1152->128 -> FC 128->10, 7 images, tensor cores), T = 1 so that every
+    layer's spikes are observable: sampled neurons of each layer are
+    recomputed by the oracle from the GPU's spikes of the layer before
+    (WeightSum + centring + multi-value bootstrap) and must match bit for
+    bit; the scores are the last layer's spikes."""
+    P, K = gpu_keys(fhe, "P630", 3)
+    _, OK = oracle_keys("P630", 3)
+    W = P["n"] + 1
+    p = 1 << P["log2_p"]
+    B = 7
+    net = synth.csnn_net(T=1)
+    imgs = synth.stroke_images(5, B).reshape(B, -1)
+    ct = fhe.encrypt(K, imgs.reshape(-1), seed=11).view(B, 28 * 28, W)
+    snn = fhe.Snn(K, net, max_images=B, variant=fhe.VARIANT_TC, use_graph=True)
+    scores = torch.empty((B, 10, W), dtype=torch.int32, device="cuda")
+    snn.infer(ct, B, scores)
+    sizes = [1152, 128, 10]
+    spk = []
+    for li, size in enumerate(sizes):
+        t = torch.empty((B, size, W), dtype=torch.int32, device="cuda")
+        snn.layer_spikes(li, t)
+        spk.append(u32(t))
+    assert np.array_equal(spk[2], u32(scores))
+    luts = O.lif_luts(P, **net["lif"])
+    x_img = u32(ct)
+    picks = [(0, 0), (3, 577), (6, 1151)]  # (image, neuron) per layer, scaled to its size
+    for li, size in enumerate(sizes):
+        rows = []
+        for img, nrn in picks:
+            nrn = nrn * size // 1152
+            layer = net["layers"][li]
+            if layer["type"] == "conv":
+                I = O.lwe_conv2d(P, layer["W"], x_img[img], layer["cin"], layer["h"], layer["w"],
+                                 layer["stride"], layer["pad"])[nrn:nrn + 1]
+            else:
+                I = O.lwe_linear(P, layer["W"][nrn:nrn + 1], spk[li - 1][img])
+            rows.append((img, nrn, O.lwe_add_const(P, I, p // 2)))
+        ref = O.pbs(P, OK, np.concatenate([r[2] for r in rows]), luts, nthreads=NTHREADS)[0]
+        for k, (img, nrn, _) in enumerate(rows):
+            assert np.array_equal(spk[li][img, nrn], ref[k]), f"layer {li} image {img} neuron {nrn}"
     assert K.status() == fhe.FHE_OK
 
 
