@@ -26,10 +26,11 @@
 //  - B = Hankel key, N = 256 output coefficients split 128 + 128 between the
 //    two CTAs of the pair.  Core matrix delta holds h[8 delta + rho + kappa];
 //    with LBO = SBO = 128 bytes the matrix descriptor walks one strip of core
-//    matrices for both the N and K directions, so one 18 KB window per
-//    (key row r, limb) feeds all 64 K16 steps of a 256-coefficient block.
-//  - D = TMEM fp32, 128 lanes (the CTA's ciphertexts) x 256 columns, double
-//    buffered (512 columns, allocated jointly by the pair).
+//    matrices for both the N and K directions, so one 10 KB window per
+//    (key row r, limb, 512 K) feeds 32 K16 steps of a 256-coefficient block.
+//  - D = TMEM fp32, 128 lanes (the CTA's ciphertexts) x 256 columns per
+//    limb; a unit accumulates two limbs, using all 512 columns (allocated
+//    jointly by the pair), so each A tile feeds two MMAs per K16 step.
 // Per SM, an M256 N256 K16 step of the pair reads 4 KB of A and 4 KB of B
 // from shared memory (64 B/clk at the tensor rate) instead of 4 + 8 KB for a
 // single-CTA M128 N256 step.
@@ -37,10 +38,11 @@
 // Cluster of 4 CTAs = 2 pairs = 256 ciphertexts.  Pair j computes output
 // polynomial j (all N coefficients, 4 limbs) for all 256 ciphertexts.  Per
 // step: digits (all warps; each CTA makes the digits of 64 ciphertexts) ->
-// units (block, limb, chunk) run by a producer warp (bulk copies), the
-// leader's MMA warp (the peer's warp 1 relays "operand landed" to the
-// leader's barriers) and eight epilogue warps per CTA (TMEM -> registers,
-// limb recombination, ACC update in global memory) -> cluster barrier.
+// cluster barrier -> units (block, limb pair, chunk) run by a digit-tile
+// producer warp, a key-window producer warp, the leader's MMA warp (the
+// peer's warp 1 relays "operand landed" to the leader's barriers) and eight
+// epilogue warps per CTA (TMEM -> registers, limb recombination, ACC update
+// in global memory) -> cluster barrier.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
