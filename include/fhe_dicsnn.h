@@ -53,6 +53,9 @@ extern "C" {
                                paper's "FFT technology", 5.3): NOT bit-exact,
                                outputs rounded from doubles; see
                                fhe_fft_max_error                              */
+#define FHE_VARIANT_AUTO 3  /* EXACT or TC per launch by batch size (same bits
+                               either way): tensor cores from the key
+                               handle's crossover up (fhe_pbs_autotune)       */
 
 /* Which key to export (fhe_keys_export / fhe_keys_size). */
 #define FHE_KEY_LWE 0  /* s:   uint32_t[n], entries 0/1                        */
@@ -160,12 +163,24 @@ void fhe_lut_free(fhe_lut *lut);
  * KeySwitch o Extract o BlindRotate o Initialize): for every input i and
  * table j, ct_out[j][i] = LWE_s(f_j(m_i)).  ct_in: device uint32[count][n+1];
  * ct_out: device uint32[L][count][n+1] (must not alias ct_in).  variant:
- * FHE_VARIANT_EXACT or FHE_VARIANT_TC (both bit-identical).  Uses the key
+ * FHE_VARIANT_EXACT, FHE_VARIANT_TC or FHE_VARIANT_AUTO (bit-identical), or
+ * FHE_VARIANT_FFT (decrypts the same, not bit-identical).  Uses the key
  * handle's workspace; batches above its capacity run in chunks.
  * Errors: FHE_EINVAL, FHE_EUNSUPPORTED (variant not built for these
  * parameters), FHE_ECUDA. */
 int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                   uint32_t *ct_out, int variant, void *stream);
+
+/* Autotuner of FHE_VARIANT_AUTO (no counterpart in the paper): times the
+ * CUDA-core and tensor-core blind rotations on this device for batches of
+ * 128, 256, ... ciphertexts (up to 4096 and the workspace), and stores in the
+ * key handle the smallest batch from which the tensor-core path is faster
+ * (written to *tc_min_batch; UINT64_MAX when the tensor-core path is not
+ * built for these parameters).  Before tuning, AUTO uses tensor cores from
+ * 1024 ciphertexts.  Synchronous; allocates and frees temporary buffers;
+ * takes seconds (longest at N = 2048).  Errors: FHE_EINVAL, FHE_ENOMEM,
+ * FHE_ECUDA, FHE_ETIMEOUT. */
+int fhe_pbs_autotune(fhe_keys *keys, uint64_t *tc_min_batch, void *stream);
 
 /* Bootstrapping that allocates nothing (no counterpart in the paper: an
  * integration aid).  Some callers cannot call cudaMalloc at the point where

@@ -121,6 +121,10 @@ struct fhe_keys {
   size_t ws_cap;         // ciphertexts per chunk
   uint32_t *d_big;       // [2][ws_cap][kN+1] extracted LWE_z ciphertexts
   int *d_status;         // device status word (FHE_OK / FHE_ETIMEOUT)
+  // FHE_VARIANT_AUTO: batches of at least tc_min_batch ciphertexts run on
+  // tensor cores, smaller ones on CUDA cores (SIZE_MAX: tensor-core path
+  // not built for these parameters); set by fhe_pbs_autotune
+  size_t tc_min_batch;
   // tensor-core key layout (built on first use of FHE_VARIANT_TC)
   void *d_bsk_tc;
   size_t bsk_tc_bytes;
@@ -180,6 +184,7 @@ int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const
 // Builds the variant's key layout and workspace ahead of the first call
 // (FHE_OK for variants without one; FHE_EUNSUPPORTED for unsupported sets).
 int pbs_prepare(fhe_keys *K, int variant);
+bool tc_available(const Params &P);
 int key_switch_batch(const fhe_keys *K, const uint32_t *d_big, size_t count, uint32_t *ct_out,
                      cudaStream_t st);
 }  // namespace fhe

@@ -184,6 +184,8 @@ extern "C" int fhe_keygen_from_seed(const fhe_params *prm, uint64_t seed, size_t
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaGetDevice(&K->device) != cudaSuccess) { free(K); return FHE_ECUDA; }
   K->ws_cap = max_batch ? max_batch : 16384;
+  // until fhe_pbs_autotune measures it: tensor cores from four cluster tiles up
+  K->tc_min_batch = fhe::tc_available(P) ? 1024u : SIZE_MAX;
   const uint64_t bsk_words = (uint64_t)P.n * P.ggsw_words();
   const uint64_t ksk_words = (uint64_t)P.k * P.N * P.l_ks * (P.n + 1u);
   bool ok = cudaMalloc(&K->d_lwe_key, sizeof(uint32_t) * P.n) == cudaSuccess &&

@@ -479,6 +479,8 @@ int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const
 int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
             uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st) {
   if (!count) return FHE_OK;
+  if (variant == FHE_VARIANT_AUTO)  // both exact paths give the same bits
+    variant = (count >= K->tc_min_batch) ? FHE_VARIANT_TC : FHE_VARIANT_EXACT;
   if (variant == FHE_VARIANT_EXACT) return pbs_exact(K, ct_in, count, lut, ct_out, table_stride, st);
   if (variant == FHE_VARIANT_TC) return pbs_tc(K, ct_in, count, lut, ct_out, table_stride, st);
   if (variant == FHE_VARIANT_FFT) return pbs_fft(K, ct_in, count, lut, ct_out, table_stride, st);

@@ -47,6 +47,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fhe_internal.cuh"
 
 using fhe::Params;
@@ -778,8 +780,11 @@ int tc_prepare(fhe_keys *K) {
   return FHE_OK;
 }
 
+bool tc_available(const Params &P) { return tc_supported(P); }
+
 int pbs_prepare(fhe_keys *K, int variant) {
   if (variant == FHE_VARIANT_FFT) return fft_prepare(K);
+  if (variant == FHE_VARIANT_AUTO) return tc_supported(K->P) ? tc_prepare(K) : FHE_OK;
   if (variant != FHE_VARIANT_TC) return FHE_OK;
   if (!tc_supported(K->P)) return FHE_EUNSUPPORTED;
   return tc_prepare(K);
@@ -823,3 +828,67 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
 }
 
 }  // namespace fhe
+
+// Autotuner of FHE_VARIANT_AUTO: both bit-exact blind rotations are timed on
+// this device for doubling batch sizes; the tensor-core path (256 ciphertexts
+// per 4-SM cluster, a fixed CMux latency per tile) wins from some batch size
+// on, the CUDA-core path (4 ciphertexts per CTA) below it.
+extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *stream) {
+  if (!K || !tc_min_batch) return FHE_EINVAL;
+  const fhe::Params &P = K->P;
+  if (!fhe::tc_available(P)) {
+    K->tc_min_batch = SIZE_MAX;
+    *tc_min_batch = UINT64_MAX;
+    return FHE_OK;
+  }
+  int rc = fhe::pbs_prepare(K, FHE_VARIANT_TC);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cmax = (K->ws_cap < 4096u) ? K->ws_cap : 4096u;
+  const uint32_t W = P.n + 1u;
+  std::vector<int32_t> f(P.p());
+  for (uint32_t u = 0; u < P.p(); ++u) f[u] = (int32_t)u;
+  fhe_lut *lut = nullptr;
+  rc = fhe_lut_create(K, f.data(), 1u, &lut);
+  if (rc) return rc;
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // the blind rotation's cost does not depend on the ciphertext values
+  bool ok = cudaMalloc(&d_in, sizeof(uint32_t) * cmax * W) == cudaSuccess &&
+            cudaMalloc(&d_out, sizeof(uint32_t) * cmax * W) == cudaSuccess &&
+            cudaMemsetAsync(d_in, 0, sizeof(uint32_t) * cmax * W, st) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  size_t best = SIZE_MAX;
+  int wins = 0;
+  for (size_t c = 128; ok && rc == FHE_OK && c <= cmax; c *= 2) {
+    float t[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && rc == FHE_OK; ++v) {
+      const int variant = v ? FHE_VARIANT_TC : FHE_VARIANT_EXACT;
+      rc = fhe::pbs_run(K, d_in, c, lut, d_out, c * W, variant, st);  // warm-up
+      if (rc) break;
+      ok = cudaEventRecord(e0, st) == cudaSuccess;
+      rc = fhe::pbs_run(K, d_in, c, lut, d_out, c * W, variant, st);
+      ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&t[v], e0, e1) == cudaSuccess;
+    }
+    if (!ok || rc) break;
+    if (t[1] <= t[0]) {
+      if (best == SIZE_MAX) best = c;
+      if (++wins == 2) break;  // the tensor-core path only gains with size
+    } else {
+      best = SIZE_MAX;
+      wins = 0;
+    }
+  }
+  if (!ok && rc == FHE_OK) { (void)cudaGetLastError(); rc = FHE_ECUDA; }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  fhe_lut_free(lut);
+  if (rc) return rc;
+  // tensor cores never won up to cmax: use them only above it
+  K->tc_min_batch = (best == SIZE_MAX) ? 2 * cmax : best;
+  *tc_min_batch = K->tc_min_batch;
+  return fhe_status(K, stream);
+}

@@ -147,7 +147,7 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   if (!K || !d || !out || !d->layers || d->n_layers == 0 || d->T == 0 || d->max_images == 0)
     return FHE_EINVAL;
   if (d->variant != FHE_VARIANT_EXACT && d->variant != FHE_VARIANT_TC &&
-      d->variant != FHE_VARIANT_FFT)
+      d->variant != FHE_VARIANT_FFT && d->variant != FHE_VARIANT_AUTO)
     return FHE_EINVAL;
   if (d->lif_mode != FHE_LIF_MULTI_VALUE && d->lif_mode != FHE_LIF_TWO_PBS) return FHE_EINVAL;
   if (d->lif_mode == FHE_LIF_TWO_PBS && d->spike_scale != 2) return FHE_EINVAL;

@@ -23,6 +23,7 @@ FHE_EUNSUPPORTED = -5
 VARIANT_EXACT = 0
 VARIANT_TC = 1
 VARIANT_FFT = 2
+VARIANT_AUTO = 3
 KEY_LWE, KEY_GLWE, KEY_BSK, KEY_KSK = 0, 1, 2, 3
 LAYER_FC, LAYER_CONV, LAYER_POISSON = 0, 1, 2
 LIF_MULTI_VALUE, LIF_TWO_PBS = 0, 1
@@ -37,7 +38,7 @@ EXPORTED = (
     "fhe_snn_layer_spikes", "fhe_snn_profile", "fhe_kernel_launches",
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
-    "fhe_snn_stream_push", "fhe_snn_stream_flush",
+    "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
 )
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
@@ -126,6 +127,7 @@ def lib():
             "fhe_fft_max_error": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
             "fhe_snn_stream_push": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
             "fhe_snn_stream_flush": (ctypes.c_int, [vp, vp]),
+            "fhe_pbs_autotune": (ctypes.c_int, [vp, ctypes.POINTER(u64), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -213,6 +215,13 @@ class Keys:
 
     def status(self, stream=None):
         return lib().fhe_status(self.handle, _stream(stream))
+
+    def autotune(self, stream=None):
+        """fhe_pbs_autotune: smallest batch run on tensor cores by
+        VARIANT_AUTO, measured on this device (None: not available)."""
+        v = ctypes.c_uint64()
+        _check(lib().fhe_pbs_autotune(self.handle, ctypes.byref(v), _stream(stream)), "pbs_autotune")
+        return None if v.value == (1 << 64) - 1 else int(v.value)
 
 
 def keygen_from_seed(params, seed, max_batch=0, stream=None):

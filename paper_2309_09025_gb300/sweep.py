@@ -1,7 +1,7 @@
 """Batched-PBS throughput sweep (one JSON line per batch size and variant).
 
     python -m paper_2309_09025_gb300.sweep [--params P630] [--batches 256,1024,4096,16384,65536]
-                                           [--variants exact,tc] [--reps 3]
+                                           [--variants exact,tc,fft,auto] [--reps 3]
 
 Uniform random messages of Z_64 bootstrapped with the identity-plus-threshold
 table f(u) = (u + [u >= p/2]) mod p through fhe_pbs_batch; the ciphertexts
@@ -36,7 +36,10 @@ def main():
     lut = fhe.lut_create(keys, synth.identity_plus_threshold_lut(p)[None])
     macs = P["n"] * (P["k"] + 1) ** 2 * P["l"] * P["N"] ** 2
     for variant in args.variants.split(","):
-        v = {"exact": fhe.VARIANT_EXACT, "tc": fhe.VARIANT_TC, "fft": fhe.VARIANT_FFT}[variant]
+        v = {"exact": fhe.VARIANT_EXACT, "tc": fhe.VARIANT_TC, "fft": fhe.VARIANT_FFT,
+             "auto": fhe.VARIANT_AUTO}[variant]
+        if variant == "auto":
+            print(json.dumps({"params": args.params, "autotune_tc_min_batch": keys.autotune()}), flush=True)
         for batch in batches:
             msgs = synth.uniform_messages(args.seed + batch, batch, p)
             ct = fhe.encrypt(keys, msgs, seed=1000 + batch)

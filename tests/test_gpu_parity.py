@@ -360,3 +360,51 @@ def test_snn_toy_layer_fft_decrypts_like_plain(fhe, oracle_keys):
     snn.infer(torch.from_numpy(ct.view(np.int32)).cuda(), 1, scores)
     plain = O.snn_plain(P, net, x)
     assert np.array_equal(O.decrypt(P, OK, u32(scores)[0]), plain["scores"])
+
+
+@pytest.mark.parametrize("name", ["P630", "P64"])
+def test_autotuned_variant_is_bit_exact(fhe, oracle_keys, name):
+    """FHE_VARIANT_AUTO picks the CUDA-core or tensor-core blind rotation by
+    batch size (crossover measured by fhe_pbs_autotune); on both sides of the
+    crossover the outputs equal the CUDA-core path's bit for bit.  P64 has no
+    tensor-core path: the tuner reports none and AUTO stays on CUDA cores."""
+    P, K = gpu_keys(fhe, name, 3)
+    p = 1 << P["log2_p"]
+    cross = K.autotune()
+    if name == "P64":
+        assert cross is None
+    else:
+        assert cross is not None and 128 <= cross <= 8192
+    luts = _luts(P, 2)
+    lut = fhe.lut_create(K, luts)
+    for count in (100, 1500):
+        m = synth.uniform_messages(51 + count, count, p)
+        ct = fhe.encrypt(K, m, seed=13)
+        ref = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
+        got = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_AUTO))
+        assert np.array_equal(got, ref)
+    assert K.status() == fhe.FHE_OK
+
+
+def test_p750_thousand_bootstraps_match_oracle_hashes(fhe):
+    """1000 bootstraps at P750 (N = 2048; keys, messages and encryption from
+    seed 4; identity-plus-threshold table) on both integer blind-rotation
+    paths: every output ciphertext equals the oracle's, compared through the
+    SHA-256 prefixes that tests/golden/make_p750_pbs_hashes.py wrote from the
+    oracle alone."""
+    import hashlib
+    path = os.path.join(os.path.dirname(__file__), "golden", "p750_pbs_1000.txt")
+    golden = [l.split()[1] for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(golden) == 1000
+    P, K = gpu_keys(fhe, "P750", 4)
+    p = 1 << P["log2_p"]
+    m = synth.uniform_messages(4, 1000, p)
+    ct = fhe.encrypt(K, m, seed=4)
+    lut = fhe.lut_create(K, synth.identity_plus_threshold_lut(p)[None])
+    for variant in VARIANTS:
+        out = u32(pbs(fhe, K, ct, lut, variant))[0]
+        got = [hashlib.sha256(np.ascontiguousarray(out[i], dtype="<u4").tobytes()).hexdigest()[:16]
+               for i in range(1000)]
+        bad = [i for i in range(1000) if got[i] != golden[i]]
+        assert not bad, f"{variant}: {len(bad)} outputs differ from the oracle, first {bad[:5]}"
+    assert K.status() == fhe.FHE_OK
