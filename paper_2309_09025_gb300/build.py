@@ -63,15 +63,11 @@ def build(force=False, verbose=False):
         for _, log in results:
             print(log)
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcuda"]
+    # runtime API only (no driver-API calls), so no -lcuda
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        # libcuda is only needed for the tensor-map encoder; link without it
-        # when the driver stub is missing (it is resolved at run time instead)
-        cmd = cmd[:-1]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
     return LIB
 
