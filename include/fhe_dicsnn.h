@@ -338,7 +338,9 @@ uint32_t fhe_snn_iterations(const fhe_snn *net);
  * pushed batch completes, synchronizes `stream` when any destination is host
  * memory (returning the device status), and ends the stream.  While a stream
  * runs, fhe_snn_infer / fhe_snn_begin return FHE_EINVAL (and vice versa);
- * fhe_snn_profile covers the launches since the stream's first push.
+ * fhe_snn_profile covers the launches since the stream's first push (with
+ * profiling on, two events are kept per bootstrap launch of the stream:
+ * meant for bounded measurement runs, not for unbounded serving).
  * Errors: FHE_EINVAL, FHE_ENOMEM (first push allocates the stream state),
  * FHE_ECUDA, FHE_ETIMEOUT. */
 int fhe_snn_stream_push(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
