@@ -125,6 +125,9 @@ struct fhe_keys {
   // tensor cores, smaller ones on CUDA cores (SIZE_MAX: tensor-core path
   // not built for these parameters); set by fhe_pbs_autotune
   size_t tc_min_batch;
+  // clusters of 8 CTAs of the tensor-core kernel the device holds at once
+  // (-1: not queried yet)
+  int tc_cl8_max;
   // tensor-core key layout (built on first use of FHE_VARIANT_TC)
   void *d_bsk_tc;
   size_t bsk_tc_bytes;

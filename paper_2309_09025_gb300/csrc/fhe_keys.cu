@@ -186,6 +186,7 @@ extern "C" int fhe_keygen_from_seed(const fhe_params *prm, uint64_t seed, size_t
   K->ws_cap = max_batch ? max_batch : 16384;
   // until fhe_pbs_autotune measures it: tensor cores from four cluster tiles up
   K->tc_min_batch = fhe::tc_available(P) ? 1024u : SIZE_MAX;
+  K->tc_cl8_max = -1;
   const uint64_t bsk_words = (uint64_t)P.n * P.ggsw_words();
   const uint64_t ksk_words = (uint64_t)P.k * P.N * P.l_ks * (P.n + 1u);
   bool ok = cudaMalloc(&K->d_lwe_key, sizeof(uint32_t) * P.n) == cudaSuccess &&

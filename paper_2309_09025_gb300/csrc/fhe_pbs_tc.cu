@@ -55,7 +55,6 @@ using fhe::Params;
 
 namespace {
 
-constexpr int kCluster = 4;       // two CTA pairs
 constexpr int kBt = 256;          // ciphertexts per cluster (MMA M of a CTA pair)
 constexpr int kBh = 128;          // ciphertexts per CTA (its half of M)
 constexpr int kBN = 256;          // output coefficients per block (MMA N)
@@ -283,8 +282,11 @@ __host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) 
   return 2ull * RR * (N / kKB) * (kATile / 2);
 }
 
-template <int N>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
+// CL = CTAs per cluster: 4 (two pairs, one per output polynomial) or 8 (four
+// pairs, each with half the blocks of one polynomial: half the work per CTA
+// and step, for batches that fit in the 15 clusters of 8 the GPU holds).
+template <int N, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
                       const uint32_t *__restrict__ ct_in, size_t count, TcLut lut,
                       uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
@@ -295,8 +297,11 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   constexpr uint32_t KH = N / kBK;               // B windows per digit row
   constexpr uint32_t KT = kBK / kKB;             // A tiles per B window
   constexpr uint32_t TILE_H = kATile / 2;        // fp16 elements of one A tile
+  constexpr uint32_t NP = CL / 2;                 // CTA pairs per cluster
+  constexpr uint32_t PPJ = NP / 2;                // pairs per output polynomial
+  constexpr uint32_t RPC = kBh / NP;              // digit rows each CTA of a half makes
   constexpr uint32_t G = 4096u / N;              // ciphertexts per staged group (32 KB)
-  constexpr uint32_t NGROUP = 64u / G;
+  constexpr uint32_t NGROUP = RPC / G;
   extern __shared__ __align__(1024) unsigned char smem[];
   const TcSmem S = tc_smem();
   unsigned char *sA = smem + S.a;
@@ -308,16 +313,18 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t *g_full = b_full + 9;  // staging buffers of the digit phase
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
-  __shared__ uint32_t s_abar[64];  // a~_i of the 64 ciphertexts whose digits this CTA makes
+  __shared__ uint32_t s_abar[RPC];  // a~_i of the ciphertexts whose digits this CTA makes
 
   const uint32_t n = P.n, l = P.l, R = 2u * l;
   const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
   const uint32_t q = cluster_rank();
-  const uint32_t pj = q / 2u;               // pair index = output polynomial j
+  const uint32_t pr = q / 2u;               // pair index
+  const uint32_t pj = pr / PPJ;             // output polynomial of the pair
+  const uint32_t bsub = pr % PPJ;           // which share of the blocks
   const uint32_t hh = q % 2u;               // ciphertext half (MMA rows 128 hh ..)
   const uint32_t lead = q & ~1u;            // rank of the pair's leader (issues the MMAs)
   const bool leader = (hh == 0u);
-  const uint64_t tile = blockIdx.x / kCluster;
+  const uint64_t tile = blockIdx.x / CL;
   const size_t base = (size_t)tile * kBt;
   // With sub_shift > 0 every gadget digit d is split into two signed
   // sub-digits d = hi * 2^sub_shift + lo (rows r and R + r of the digit
@@ -327,17 +334,21 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);           // [256][2][N]
   __half *dig = dig_g + tile * tc_tile_dig_halves(N, RR);
   __half *dig_h = dig + (uint64_t)hh * RR * KBLK * TILE_H;        // this half's digit rows
-  const uint32_t row0 = kBh * hh + 64u * pj;  // first ciphertext whose digits this CTA makes
-  const uint32_t nblk = N / kBN;              // blocks of 256 output coefficients
+  const uint32_t row0 = kBh * hh + RPC * pr;  // first ciphertext whose digits this CTA makes
+  const uint32_t nblk = N / kBN / PPJ;        // blocks of 256 output coefficients of this pair
+  const uint32_t blk0 = bsub * nblk;
   const uint32_t nchunk = RR / chunk_r;
   const uint64_t strip_halves = (uint64_t)(N / 4u) * 64u;
   const uint16_t pair_mask = (uint16_t)(3u << lead);
-  const uint16_t a_mask = (uint16_t)((1u << q) | (1u << (q ^ 2u)));
+  // every CTA of the same half receives the digit rows this CTA makes
+  uint16_t a_mask = 0;
+  for (uint32_t k = 0; k < NP; ++k) a_mask |= (uint16_t)(1u << (2u * k + hh));
+  const uint16_t all_mask = (uint16_t)((1u << CL) - 1u);
 
   if (tid == 0) {
     s_abort = 0;
     for (uint32_t s = 0; s < kAStages; ++s) {
-      mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 2); mbar_init(&a_peer[s], 1);
+      mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], NP); mbar_init(&a_peer[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); mbar_init(&b_peer[s], 1);
@@ -353,9 +364,9 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                  "r"((uint32_t)kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
-  // initial accumulators of this CTA's 64 ciphertexts: (0, X^{-b~} TV)
+  // initial accumulators of this CTA's RPC ciphertexts: (0, X^{-b~} TV)
   const uint32_t half_delta = P.delta() >> 1;
-  for (uint32_t e = tid; e < 64u * N; e += kThreads) {
+  for (uint32_t e = tid; e < RPC * N; e += kThreads) {
     const uint32_t b = row0 + e / N, c = e % N;
     const uint32_t v_ct = (base + b < count) ? ct_in[(base + b) * (n + 1u) + n] : 0u;
     const uint32_t bb = fhe::mod_switch_2n(v_ct, LOG2_2N);
@@ -381,12 +392,12 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t a_it = 0, b_it = 0, u_it = 0, g_it = 0;
 
   for (uint32_t i = 0; i < n; ++i) {
-    // ---- digits of X^{a~_i} ACC - ACC for this CTA's 64 ciphertexts.
+    // ---- digits of X^{a~_i} ACC - ACC for this CTA's RPC ciphertexts.
     // Groups of G ciphertexts (both polynomials, 32 KB) are staged in shared
     // memory by bulk copies, kGBuf groups in flight.  One warp per chunk of 256
     // coefficients of one polynomial; lane L owns c = c_base + 32k + L, so
     // shared-memory reads are conflict free and global stores coalesced.
-    if (tid < 64u) {
+    if (tid < RPC) {
       const uint32_t b = row0 + tid;
       const uint32_t av = (base + b < count) ? __ldg(ct_in + (base + b) * (n + 1u) + i) : 0u;
       s_abar[tid] = fhe::mod_switch_2n(av, LOG2_2N);
@@ -413,8 +424,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
       constexpr uint32_t ITEMS = G * 2u * NB;  // = 32
       for (uint32_t item = warp; got && item < ITEMS; item += kThreads / 32u) {
         const uint32_t cb = item % NB, j = (item / NB) & 1u, gi = item / (2u * NB);
-        const uint32_t bl = g * G + gi;             // 0..63
-        const uint32_t bm = 64u * pj + bl;          // MMA row within this half
+        const uint32_t bl = g * G + gi;             // 0..RPC-1
+        const uint32_t bm = RPC * pr + bl;          // MMA row within this half
         const uint32_t a = s_abar[bl];
         const uint32_t *Pj = sacc + (gi * 2u + j) * N;
         uint32_t xr[2][4];
@@ -524,7 +535,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
     if (warp == 0 || warp == kBWarp) {
       // producers: warp 0 streams the digit tiles, warp kBWarp the key windows
       if (lane == 0) {
-        for (uint32_t blk = 0; blk < nblk; ++blk) {
+        for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
           const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
           for (uint32_t lp = 0; lp < 2u; ++lp)
             for (uint32_t ch = 0; ch < nchunk; ++ch)
@@ -551,9 +562,9 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                     if (a_it >= kAStages)
                       wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
                     if (!s_abort) {
-                      const __half *src = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H + pj * (TILE_H / 2u);
+                      const __half *src = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H + pr * (TILE_H / NP);
                       mbar_expect_tx(&a_full[as], kATile);
-                      bulk_g2s_multicast(sA + as * kATile + pj * (kATile / 2), src, kATile / 2,
+                      bulk_g2s_multicast(sA + as * kATile + pr * (kATile / NP), src, kATile / NP,
                                          &a_full[as], a_mask);
                     }
                     ++a_it;
@@ -564,7 +575,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
       __syncwarp();
     } else if (warp == 1) {
       if (lane == 0 && leader) {
-        for (uint32_t blk = 0; blk < nblk; ++blk)
+        for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t lp = 0; lp < 2u; ++lp)
             for (uint32_t ch = 0; ch < nchunk; ++ch) {
               if (u_it >= 1u) wait_bounded(t_empty, (u_it - 1u) & 1u, &s_abort);
@@ -594,7 +605,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
                         }
                         accum = 1u;
                       }
-                      tc2_commit_multicast(&a_empty[as], (uint16_t)0xFu);
+                      tc2_commit_multicast(&a_empty[as], all_mask);
                     }
                     ++a_it;
                   }
@@ -607,7 +618,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
       } else if (lane == 0) {
         // peer: tell the leader when this CTA's halves of A and B have landed
         const uint32_t bp0 = cluster_addr(&b_peer[0], lead), bp1 = cluster_addr(&b_peer[1], lead);
-        for (uint32_t blk = 0; blk < nblk; ++blk)
+        for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t lp = 0; lp < 2u; ++lp)
             for (uint32_t ch = 0; ch < nchunk; ++ch)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
@@ -631,7 +642,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
       const uint32_t quarter = warp % 4u, half = (warp - 2u) / 4u;
       const uint32_t row = kBh * hh + 32u * quarter + lane;  // ciphertext row of the tile
       const uint32_t te = cluster_addr(t_empty, lead);
-      for (uint32_t blk = 0; blk < nblk; ++blk) {
+      for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
         uint32_t *dst = acc + ((uint64_t)row * 2u + pj) * N + blk * kBN + half * 128u;
         uint32_t outv[128];
         // ACC of this block, loaded while the block's MMAs run
@@ -691,7 +702,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t W = N + 1u;
   for (uint32_t jl = 0; jl < lut.L; ++jl) {
     const uint32_t nnz = jl ? lut.nnz1 : lut.nnz0, off = jl ? lut.off1 : lut.off0;
-    for (uint32_t e = tid; e < 64u * W; e += kThreads) {
+    for (uint32_t e = tid; e < RPC * W; e += kThreads) {
       const uint32_t b = row0 + e / W, c = e % W;
       if (base + b >= count) continue;
       const uint32_t *A = acc + ((uint64_t)b * 2u) * N;
@@ -805,14 +816,28 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   la.off0 = lut->off[0]; la.off1 = lut->off[1];
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem();
-  auto kern = (P.N == 1024u) ? k_blind_rotate_tc<1024> : k_blind_rotate_tc<2048>;
-  FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  auto kern4 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 4> : k_blind_rotate_tc<2048, 4>;
+  auto kern8 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 8> : k_blind_rotate_tc<2048, 8>;
+  FHE_CUDA_TRY(cudaFuncSetAttribute(kern4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  FHE_CUDA_TRY(cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  if (K->tc_cl8_max < 0) {  // clusters of 8 the device holds at once (once per key handle)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(8);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = S.total;
+    int n8 = 0;
+    if (cudaOccupancyMaxActiveClusters(&n8, kern8, &cfg) != cudaSuccess) { (void)cudaGetLastError(); n8 = 0; }
+    K->tc_cl8_max = n8;
+  }
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
     const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
+    // a batch that fits in one wave of 8-CTA clusters runs with half the work
+    // per CTA and step (lower latency); larger ones use the 36 clusters of 4
+    const bool eight = (int)tiles <= K->tc_cl8_max;
     const bool prof = (s0 == 0) && K->prof_ev0;
     if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
-    kern<<<tiles * kCluster, kThreads, S.total, st>>>(
+    (eight ? kern8 : kern4)<<<tiles * (eight ? 8u : 4u), kThreads, S.total, st>>>(
         P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
         (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status);
     note_launches(1);
