@@ -33,6 +33,9 @@ def main():
     ap.add_argument("--params", default="P630")
     ap.add_argument("--batches", type=int, default=3)
     ap.add_argument("--only", default="csnn,csnn_two_pbs,paper_csnn,poisson")
+    ap.add_argument("--latency", action="store_true",
+                    help="one image per call through fhe_snn_infer (graphs, AUTO variant): "
+                         "latency of a single encrypted prediction")
     args = ap.parse_args()
     build.build()
     P = dict(synth.PRESETS[args.params])
@@ -51,6 +54,28 @@ def main():
     stream = torch.cuda.current_stream()
     for name in args.only.split(","):
         net, neurons, gen = nets[name]
+        if args.latency:
+            keys.autotune()
+            snn = fhe.Snn(keys, net, max_images=1, variant=fhe.VARIANT_AUTO, use_graph=True)
+            img = gen(5, 1).reshape(1, -1)
+            ct1 = fhe.encrypt(keys, img.reshape(-1), seed=11).view(1, 28 * 28, W)
+            sc = torch.empty((1, 10, W), dtype=torch.int32, device="cuda")
+            snn.infer(ct1, 1, sc)  # captures the graphs
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.batches):
+                snn.infer(ct1, 1, sc)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.batches
+            print(json.dumps({"workload": name, "params": args.params, "T": net["T"], "images": 1,
+                              "pbs_per_image": snn.pbs_per_image(), "ms_per_prediction": ms,
+                              "pbs_per_s": snn.pbs_per_image() / (ms / 1e3), "status": keys.status()}),
+                  flush=True)
+            snn.free()
+            continue
         B = max(1, 9216 // neurons)
         snn = fhe.Snn(keys, net, max_images=B, variant=fhe.VARIANT_TC, use_graph=False, profile=True)
         per_image = snn.pbs_per_image()
