@@ -235,12 +235,13 @@ def test_snn_csnn_topology_small_params_bit_exact(fhe, oracle_keys):
         assert np.array_equal(scores[i], ref["scores"])
 
 
-@pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 613)])
+@pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 613), ("P630", 3999), ("P750", 3999)])
 def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
     """Tensor-core blind rotation: every output of a multi-cluster batch
     (ragged against 256-ciphertext cluster tiles) bit-identical to the
     CUDA-core path, outputs at the tile edges bit-identical to the oracle, for
-    both table counts (P750: N = 2048 with split sub-digits)."""
+    both table counts (P750: N = 2048 with split sub-digits).  Up to 15 tiles
+    run on clusters of 8 CTAs, 16 tiles (3999 ciphertexts) on clusters of 4."""
     P, K = gpu_keys(fhe, name, 3)
     _, OK = oracle_keys(name, 3)
     p = 1 << P["log2_p"]
