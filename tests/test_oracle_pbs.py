@@ -212,3 +212,38 @@ def test_test_poly_box_lookup():
         box = ((2 * phi * p + N) // (2 * N)) % (2 * p)  # round(phi p / N) mod 2p
         val = int(f[box]) * d if box < p else -int(f[box - p]) * d
         assert int(_rot_expected(tv, phi)[0]) == val & MASK32
+
+
+def test_multi_value_output_noise(oracle_keys):
+    """Multi-value PBS output error (4.3: one rotation of TV0, then r_j * ACC,
+    extraction, key switch).  r_j * X^(-phi~) TV0 = X^(-phi~) Delta coeffs_j, so
+    the noiseless phase is coefficient 0 of X^(-phi~) TV_j; the error is
+    (r_j * E_BR)[0] + e_KS with variance ||r_j||^2 Var_BR + Var_KS.  The sample
+    variance of the error, each sample scaled by its predicted standard
+    deviation, lies within [0.7, 1.3] of 1."""
+    P, K = oracle_keys("P64", 13)
+    p = 1 << P["log2_p"]
+    n, kN = P["n"], P["k"] * P["N"]
+    luts = O.lif_luts(P, v_th=8, leak_shift=1, spike_scale=1)
+    g = np.random.default_rng(17)
+    m = g.integers(0, p, 600).astype(np.int32)
+    ct = O.encrypt(P, K, m, 4242)
+    out = O.pbs(P, K, ct, luts)
+    Bks = 2 ** P["log2_bks"]
+    sig = 2.0 ** (32 - P["lwe_noise_log2"])
+    var_ks = kN / 2 * (2.0 ** (32 - P["l_ks"] * P["log2_bks"])) ** 2 / 12 \
+        + kN * P["l_ks"] * (Bks ** 2 + 2) / 12 * sig ** 2
+    scaled = []
+    for j in range(2):
+        co = O.lut_coeffs(P, luts[j]).astype(np.int64)
+        r = np.empty_like(co)
+        r[0] = co[0] + co[-1]
+        r[1:] = co[1:] - co[:-1]
+        var = float((r * r).sum()) * _br_noise_var(P) + var_ks
+        tv = O.test_poly(P, luts[j])
+        ph = O.phase(P, K, out[j]).astype(np.int64)
+        for i in range(len(m)):
+            exp = int(_rot_expected(tv, _exact_phase_tilde(P, K, ct[i]))[0])
+            scaled.append(float(_signed(int(ph[i]) - exp)) / np.sqrt(var))
+    ratio = float(np.var(scaled))
+    assert 0.7 < ratio < 1.3, ratio
