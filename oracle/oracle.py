@@ -62,7 +62,8 @@ def lib():
             "orc_sample_extract": (None, [pp, u32p, u32p]),
             "orc_key_switch": (None, [pp, u32p, u32p, u32p]),
             "orc_pbs": (None, [pp, u32p, u32p, u32p, i32p, u32, u32p]),
-            "orc_pbs_batch": (None, [pp, u32p, u32p, u32p, u64, i32p, u32, u32p, ctypes.c_int]),
+            "orc_pbs_batch": (None, [pp, u32p, u32p, u32p, u64, i32p, u32, u32p, u32p,
+                                     ctypes.c_int]),
             "orc_lwe_linear": (None, [u32, u32, i32p, u64, u64, i32p, u32p, u32p]),
             "orc_lwe_conv2d": (None, [u32, u32, u32, u32, u32, u32, u32, u32, u32, u32,
                                       i32p, i32p, u32p, u32p]),
@@ -218,8 +219,10 @@ def key_switch(P, keys, big):
     return out
 
 
-def pbs(P, keys, ct, luts, nthreads=None):
-    """Batched bootstrapping; luts is (L, p); returns (L, count, n+1)."""
+def pbs(P, keys, ct, luts, nthreads=None, log2_p_out=None):
+    """Batched bootstrapping; luts is (L, p) with p = 2^P['log2_p'], the
+    input's message space; table j is written with Delta = 2^(31 -
+    log2_p_out[j]) (default: the input's space).  Returns (L, count, n+1)."""
     luts, pl = _i32(np.asarray(luts).reshape(-1, 1 << P["log2_p"]))
     L = luts.shape[0]
     ct, pc = _u32(np.asarray(ct).reshape(-1, P["n"] + 1))
@@ -227,8 +230,13 @@ def pbs(P, keys, ct, luts, nthreads=None):
     out = np.zeros((L, count, P["n"] + 1), np.uint32)
     if nthreads is None:
         nthreads = os.cpu_count() or 1
+    po = ctypes.POINTER(ctypes.c_uint32)()
+    if log2_p_out is not None:
+        lp = np.asarray(log2_p_out, np.uint32).reshape(-1)
+        assert lp.shape[0] == L and lp.min() >= 1 and lp.max() <= 30
+        lp, po = _u32(lp)
     lib().orc_pbs_batch(_p(P), _u32(keys["bsk"])[1], _u32(keys["ksk"])[1], pc, count, pl, L,
-                        _u32(out)[1], int(nthreads))
+                        po, _u32(out)[1], int(nthreads))
     return out
 
 
@@ -322,17 +330,38 @@ def wrap2p(x, p):
     return ((x + p) % (2 * p)) - p
 
 
-def plain_bootstrap(f, v, p, centre=True):
+def plain_bootstrap(f, v, p, centre=True, p_out=None):
     """What a bootstrap of a message v (mod 2p, centred by +p/2 unless
-    centre is False) decrypts to.
+    centre is False) decrypts to, read in the output space p_out (default p).
 
     u = (v + p/2) mod 2p; f(u) for u < p, -f(u - p) otherwise (negacyclic half,
-    Thm 2.1), reduced mod 2p.
+    Thm 2.1), reduced mod 2 p_out.
     """
     u = (np.asarray(v, dtype=np.int64) + (p // 2 if centre else 0)) % (2 * p)
     f = np.asarray(f, dtype=np.int64)
     out = np.where(u < p, f[np.minimum(u, p - 1)], -f[np.maximum(u - p, 0)])
-    return wrap2p(out, p)
+    return wrap2p(out, p if p_out is None else p_out)
+
+
+def layer_spaces(P, net):
+    """log2 of each layer's message space p_l (the dynamic message space of
+    DiNN carried over in 5.2): layer['log2_p'] where given, else the key's
+    P['log2_p'].  Layer l's currents, membranes and bootstrap boxes live in
+    Z_{2 p_l}; its spikes are written in the space of the layer that reads
+    them (the key's space for the last layer, whose spikes form the
+    scores).  The network input is encrypted in the key's space, so a
+    WeightSum first layer needs p_0 <= p (its weights are multiplied by
+    p / p_0 in the ciphertext domain); a Poisson first layer compares pixels
+    in the key's space itself.  Only the multi-value mode changes spaces."""
+    lps = [int(layer.get("log2_p", P["log2_p"])) for layer in net["layers"]]
+    for li, (layer, lp) in enumerate(zip(net["layers"], lps)):
+        if not 1 <= lp or (2 << lp) > P["N"]:
+            raise ValueError("layer %d: message space 2^%d does not fit N" % (li, lp))
+        if li == 0 and (lp > P["log2_p"] or (layer["type"] == "poisson" and lp != P["log2_p"])):
+            raise ValueError("first layer: message space must not exceed the input's")
+    if net.get("lif_mode") == "two_pbs" and any(lp != P["log2_p"] for lp in lps):
+        raise ValueError("the two-bootstrap mode keeps the key's message space")
+    return lps
 
 
 def _plain_layer(layer, x):
@@ -368,15 +397,23 @@ def snn_plain(P, net, inputs):
     net['lif_mode'] = 'two_pbs' evaluates the paper's separate negacyclic
     bootstraps (4.2): S = sign(H - V_th) + 1, V = g(H) without centring.  A
     'poisson' first layer (2.3) spikes where the pixel exceeds M[t]; its 'h'
-    entry is x - M[t].
+    entry is x - M[t].  Layers with their own message space (layer_spaces)
+    wrap their currents and membranes mod 2 p_l and write their spikes mod
+    2 p of the reading layer.
     """
     p = 1 << P["log2_p"]
     T = net["T"]
     lif = net["lif"]
     two = net.get("lif_mode") == "two_pbs"
-    f = lif_luts(P, lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+    lps = layer_spaces(P, net)
+    nl = len(net["layers"])
+    # p_l of each layer and the space its spikes are written in
+    pl = [1 << lp for lp in lps]
+    pn = [1 << (lps[li + 1] if li + 1 < nl else P["log2_p"]) for li in range(nl)]
+    f = [lif_luts(dict(P, log2_p=lp), lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+         for lp in lps]
     g = lif_luts_two_pbs(P, lif["v_th"], lif["leak_shift"])
-    V = [None] * len(net["layers"])
+    V = [None] * nl
     spikes = [[] for _ in net["layers"]]
     hs = [[] for _ in net["layers"]]
     static_I0 = None
@@ -384,26 +421,27 @@ def snn_plain(P, net, inputs):
         x = inputs if net.get("static_input") else inputs[t]
         for li, layer in enumerate(net["layers"]):
             if layer["type"] == "poisson":
-                S = poisson_spikes(x, layer["M"][t], 2 if two else lif["spike_scale"])
+                S = wrap2p(poisson_spikes(x, layer["M"][t], 2 if two else lif["spike_scale"]),
+                           pn[li])
                 spikes[li].append(S)
                 hs[li].append(np.asarray(x, np.int64) - np.asarray(layer["M"][t], np.int64))
                 x = S
                 continue
             if li == 0 and net.get("static_input"):
                 if static_I0 is None:
-                    static_I0 = wrap2p(_plain_layer(layer, x), p)
+                    static_I0 = wrap2p(_plain_layer(layer, x), pl[li])
                 I = static_I0
             else:
-                I = wrap2p(_plain_layer(layer, x), p)
+                I = wrap2p(_plain_layer(layer, x), pl[li])
             if V[li] is None:
                 V[li] = np.zeros_like(I)
-            H = wrap2p(V[li] + I, p)
+            H = wrap2p(V[li] + I, pl[li])
             if two:
                 S = wrap2p(plain_bootstrap(g[0], H - lif["v_th"], p, centre=False) + 1, p)
                 V[li] = plain_bootstrap(g[1], H, p, centre=False)
             else:
-                S = plain_bootstrap(f[0], H, p)
-                V[li] = plain_bootstrap(f[1], H, p)
+                S = plain_bootstrap(f[li][0], H, pl[li], p_out=pn[li])
+                V[li] = plain_bootstrap(f[li][1], H, pl[li])
             spikes[li].append(S)
             hs[li].append(H)
             x = S
@@ -423,16 +461,22 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
     (4.2).  A 'poisson' first layer bootstraps the comparison x > M[t] (2.3):
     the Fire table on x - M[t] + V_th - 1 (multi-value; its Reset output is
     not used) or the sign table on x - M[t] - 1, plus 1 (two bootstraps).
-    Returns dict(spikes=[per layer (T, size, n+1)], scores=(n_out, n+1)).
+    Per-layer message spaces (layer_spaces): layer l centres by p_l/2, reads
+    with p_l boxes and writes Fire in the reading layer's space, Reset in its
+    own.  Returns dict(spikes=[per layer (T, size, n+1)], scores=(n_out, n+1)).
     """
     p = 1 << P["log2_p"]
     w = P["n"] + 1
     T = net["T"]
     lif = net["lif"]
     two = net.get("lif_mode") == "two_pbs"
-    luts = lif_luts(P, lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+    lps = layer_spaces(P, net)
+    nl = len(net["layers"])
+    lpn = [lps[li + 1] if li + 1 < nl else P["log2_p"] for li in range(nl)]
+    Pl = [dict(P, log2_p=lp) for lp in lps]
+    luts = [lif_luts(Q, lif["v_th"], lif["leak_shift"], lif["spike_scale"]) for Q in Pl]
     g = lif_luts_two_pbs(P, lif["v_th"], lif["leak_shift"])
-    V = [None] * len(net["layers"])
+    V = [None] * nl
     spikes = [[] for _ in net["layers"]]
     static_I0 = None
     scores = None
@@ -446,16 +490,19 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
                     S = lwe_add_const(P, pbs(P, keys, Hf, g[0:1], nthreads=nthreads)[0], 1)
                 else:
                     Hc = lwe_add_consts(P, x, -M + lif["v_th"] - 1 + p // 2)
-                    S = pbs(P, keys, Hc, luts, nthreads=nthreads)[0]
+                    S = pbs(P, keys, Hc, luts[li], nthreads=nthreads,
+                            log2_p_out=[lpn[li], lps[li]])[0]
                 spikes[li].append(S)
                 x = S
                 continue
+            # the input's Delta is p / p_0 times smaller than layer 0's
+            Wl = np.asarray(layer["W"], np.int64) * (1 << (P["log2_p"] - lps[0]) if li == 0 else 1)
             if li == 0 and net.get("static_input") and static_I0 is not None:
                 I = static_I0
             elif layer["type"] == "fc":
-                I = lwe_linear(P, layer["W"], x, layer.get("bias"))
+                I = lwe_linear(Pl[li], Wl, x, layer.get("bias"))
             else:
-                I = lwe_conv2d(P, layer["W"], x, layer["cin"], layer["h"], layer["w"],
+                I = lwe_conv2d(Pl[li], Wl, x, layer["cin"], layer["h"], layer["w"],
                                layer["stride"], layer["pad"], layer.get("bias"))
             if li == 0 and net.get("static_input"):
                 static_I0 = I
@@ -467,8 +514,9 @@ def snn_encrypted(P, keys, net, ct_inputs, nthreads=None):
                 S = lwe_add_const(P, pbs(P, keys, Hf, g[0:1], nthreads=nthreads)[0], 1)
                 V[li] = pbs(P, keys, H, g[1:2], nthreads=nthreads)[0]
             else:
-                Hc = lwe_add_const(P, H, p // 2)
-                out = pbs(P, keys, Hc, luts, nthreads=nthreads)
+                Hc = lwe_add_const(Pl[li], H, (1 << lps[li]) // 2)
+                out = pbs(Pl[li], keys, Hc, luts[li], nthreads=nthreads,
+                          log2_p_out=[lpn[li], lps[li]])
                 S, V[li] = out[0], out[1]
             spikes[li].append(S)
             x = S

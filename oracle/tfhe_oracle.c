@@ -385,15 +385,23 @@ void orc_key_switch(const orc_params *P, const uint32_t *ksk, const uint32_t *bi
 }
 
 /* Programmable bootstrapping (paper Thm 2.1 and
- * bootstrapping = KeySwitch o Extract o BlindRotate o Initialize).
- * L = 1: one LUT, test polynomial TV = Delta * coeffs(f).
+ * bootstrapping = KeySwitch o Extract o BlindRotate o Initialize), from the
+ * message space p_in = 2^P->log2_p of the input into the spaces of the
+ * outputs: table j is written in the encoding Delta_j = 2^(31 - log2_p_out[j])
+ * (the dynamic message space of DiNN that the paper adopts, 5.2: a
+ * bootstrap reads its input with the boxes of one space and may write its
+ * result in another).
+ * L = 1: one LUT, test polynomial TV = Delta_0 * coeffs(f).
  * L = 2: multi-value reading of the two PBS per LIF neuron (FHE-Fire and
- *        FHE-Reset, paper 4.2): one blind rotation of TV0 = (Delta/2) sum X^i,
- *        then ACC_j = r_j * ACC with r_j = (1 - X) coeffs(f_j), because
- *        (1 - X) sum X^i = 2 mod X^N + 1 gives r_j * TV0 = Delta coeffs(f_j).
- * luts: L x p signed values; out: L consecutive LWE_s ciphertexts.       */
-void orc_pbs(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk, const uint32_t *ct,
-             const int32_t *luts, uint32_t L, uint32_t *out) {
+ *        FHE-Reset, paper 4.2): one blind rotation of
+ *        TV0 = (Delta_min / 2) sum X^i, Delta_min = min_j Delta_j, then
+ *        ACC_j = r_j * ACC with r_j = (Delta_j / Delta_min) (1 - X) coeffs(f_j),
+ *        because (1 - X) sum X^i = 2 mod X^N + 1 gives
+ *        r_j * TV0 = Delta_j coeffs(f_j).
+ * luts: L x p_in signed values; out: L consecutive LWE_s ciphertexts.    */
+void orc_pbs_spaces(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk,
+                    const uint32_t *ct, const int32_t *luts, uint32_t L,
+                    const uint32_t *log2_p_out, uint32_t *out) {
   const uint32_t N = P->N, k = P->k, n = P->n;
   const uint32_t p = 1u << P->log2_p;
   const uint64_t glwe_sz = (uint64_t)(k + 1u) * N;
@@ -404,18 +412,24 @@ void orc_pbs(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk, cons
   uint32_t *rj = (uint32_t *)malloc(sizeof(uint32_t) * N);
   int32_t *co = (int32_t *)malloc(sizeof(int32_t) * N);
   if (L == 1u) {
-    orc_test_poly(P, luts, tv);
+    const uint32_t delta_out = 1u << (31u - log2_p_out[0]);
+    orc_lut_coeffs(P, luts, co);
+    for (uint32_t c = 0; c < N; ++c) tv[c] = (uint32_t)co[c] * delta_out;
     orc_blind_rotate(P, bsk, ct, tv, acc);
     orc_sample_extract(P, acc, big);
     orc_key_switch(P, ksk, big, out);
   } else {
-    uint32_t half_delta = 1u << (30u - P->log2_p);
-    for (uint32_t c = 0; c < N; ++c) tv[c] = half_delta;
+    uint32_t log2_p_max = 0;
+    for (uint32_t j = 0; j < L; ++j)
+      if (log2_p_out[j] > log2_p_max) log2_p_max = log2_p_out[j];
+    const uint32_t half_delta_min = 1u << (30u - log2_p_max);
+    for (uint32_t c = 0; c < N; ++c) tv[c] = half_delta_min;
     orc_blind_rotate(P, bsk, ct, tv, acc);
     for (uint32_t j = 0; j < L; ++j) {
+      const uint32_t scale = 1u << (log2_p_max - log2_p_out[j]);  /* Delta_j / Delta_min */
       orc_lut_coeffs(P, luts + (uint64_t)j * p, co);
-      rj[0] = (uint32_t)co[0] + (uint32_t)co[N - 1u];
-      for (uint32_t c = 1; c < N; ++c) rj[c] = (uint32_t)co[c] - (uint32_t)co[c - 1u];
+      rj[0] = scale * ((uint32_t)co[0] + (uint32_t)co[N - 1u]);
+      for (uint32_t c = 1; c < N; ++c) rj[c] = scale * ((uint32_t)co[c] - (uint32_t)co[c - 1u]);
       for (uint32_t comp = 0; comp <= k; ++comp)
         orc_negacyclic_mul(rj, acc + (uint64_t)comp * N, N, accj + (uint64_t)comp * N);
       orc_sample_extract(P, accj, big);
@@ -430,6 +444,14 @@ void orc_pbs(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk, cons
   free(co);
 }
 
+/* Bootstrapping within the input's own message space (every table written
+ * with the input's Delta).                                               */
+void orc_pbs(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk, const uint32_t *ct,
+             const int32_t *luts, uint32_t L, uint32_t *out) {
+  uint32_t same[2] = {P->log2_p, P->log2_p};
+  orc_pbs_spaces(P, bsk, ksk, ct, luts, L, same, out);
+}
+
 /* Batched PBS over independent ciphertexts with plain worker threads (the
  * paper's "parallel computing" of bootstraps, 5.3).  out layout:
  * [L][count][n+1].                                                       */
@@ -438,6 +460,7 @@ typedef struct {
   const uint32_t *bsk, *ksk, *ct;
   const int32_t *luts;
   uint32_t L;
+  const uint32_t *log2_p_out;
   uint32_t *out;
   uint64_t count, begin, end;
 } orc_batch_job;
@@ -447,7 +470,7 @@ static void *orc_batch_worker(void *arg) {
   const uint32_t w = J->P->n + 1u;
   uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * (uint64_t)J->L * w);
   for (uint64_t idx = J->begin; idx < J->end; ++idx) {
-    orc_pbs(J->P, J->bsk, J->ksk, J->ct + idx * w, J->luts, J->L, tmp);
+    orc_pbs_spaces(J->P, J->bsk, J->ksk, J->ct + idx * w, J->luts, J->L, J->log2_p_out, tmp);
     for (uint32_t j = 0; j < J->L; ++j)
       memcpy(J->out + ((uint64_t)j * J->count + idx) * w, tmp + (uint64_t)j * w,
              sizeof(uint32_t) * w);
@@ -456,9 +479,12 @@ static void *orc_batch_worker(void *arg) {
   return NULL;
 }
 
+/* log2_p_out: L output spaces, or NULL for the input's own space.        */
 void orc_pbs_batch(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk,
                    const uint32_t *ct, uint64_t count, const int32_t *luts, uint32_t L,
-                   uint32_t *out, int nthreads) {
+                   const uint32_t *log2_p_out, uint32_t *out, int nthreads) {
+  uint32_t same[2] = {P->log2_p, P->log2_p};
+  if (!log2_p_out) log2_p_out = same;
   if (nthreads < 1) nthreads = 1;
   if ((uint64_t)nthreads > count) nthreads = (int)(count ? count : 1);
   pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
@@ -470,6 +496,7 @@ void orc_pbs_batch(const orc_params *P, const uint32_t *bsk, const uint32_t *ksk
     jobs[t].ct = ct;
     jobs[t].luts = luts;
     jobs[t].L = L;
+    jobs[t].log2_p_out = log2_p_out;
     jobs[t].out = out;
     jobs[t].count = count;
     jobs[t].begin = count * (uint64_t)t / (uint64_t)nthreads;
