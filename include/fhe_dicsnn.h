@@ -159,6 +159,24 @@ int fhe_lwe_conv2d(uint32_t n, uint32_t log2_p, const int32_t *W, uint32_t cin, 
 int fhe_lut_create(const fhe_keys *keys, const int32_t *f, uint32_t L, fhe_lut **out);
 void fhe_lut_free(fhe_lut *lut);
 
+/* Tables between message spaces (the dynamic message space of DiNN, which
+ * the paper adopts in 5.2, Parameters Selection): group g reads its input
+ * in Z_{2 p_g}, p_g = 2^log2_p_in[g] (boxes round(i p_g / N), padding
+ * Delta_in = 2^31 / p_g), and writes table j with the encoding
+ * Delta = 2^(31 - log2_p_out[g*L + j]), i.e. ct_out decrypts to f_j(m) in
+ * Z_{2 p_out}.  A multi-value group rotates TV0 = (Delta_min / 2) sum X^i,
+ * Delta_min the group's smallest output Delta, and applies
+ * r_j = (Delta_j / Delta_min) (1 - X) coeffs(f_j).  f: host int32, the
+ * groups one after another, group g holding L tables of p_g values.
+ * groups (1 .. FHE_LUT_MAX_GROUPS) > 1 only with L = 2; fhe_pbs_batch_groups
+ * says which ciphertexts use which group.  fhe_lut_create(keys, f, L, out)
+ * is one group in the key's space.  Errors: FHE_EINVAL (null pointer, L not
+ * 1 or 2, group count out of range, a log2 value outside [1, 10], or
+ * 2 p_in > N), FHE_ENOMEM, FHE_ECUDA. */
+#define FHE_LUT_MAX_GROUPS 8
+int fhe_lut_create_spaces(const fhe_keys *keys, const int32_t *f, uint32_t L, uint32_t groups,
+                          const uint32_t *log2_p_in, const uint32_t *log2_p_out, fhe_lut **out);
+
 /* Programmable bootstrapping of a batch (paper Thm 2.1, bootstrapping =
  * KeySwitch o Extract o BlindRotate o Initialize): for every input i and
  * table j, ct_out[j][i] = LWE_s(f_j(m_i)).  ct_in: device uint32[count][n+1];
@@ -170,6 +188,16 @@ void fhe_lut_free(fhe_lut *lut);
  * parameters), FHE_ECUDA. */
 int fhe_pbs_batch(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                   uint32_t *ct_out, int variant, void *stream);
+
+/* fhe_pbs_batch with a grouped table set (fhe_lut_create_spaces): inputs
+ * [seg_end[g-1], seg_end[g]) use group g (seg_end[-1] = 0; the last group
+ * runs to count).  seg_end: host size_t[groups - 1], non-decreasing, each
+ * <= count (empty groups allowed); NULL only for one group.  One launch
+ * serves every group (a network bootstraps all its layers at once).
+ * fhe_pbs_batch and fhe_pbs_batch_noalloc reject grouped sets.
+ * Errors: as fhe_pbs_batch, FHE_EINVAL for bad segment ends. */
+int fhe_pbs_batch_groups(fhe_keys *keys, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
+                         const size_t *seg_end, uint32_t *ct_out, int variant, void *stream);
 
 /* Autotuner of FHE_VARIANT_AUTO (no counterpart in the paper): times the
  * CUDA-core and tensor-core blind rotations on this device for batches of
@@ -266,6 +294,17 @@ typedef struct fhe_layer_desc {
   uint32_t in_size;        /* FC, Poisson: number of inputs                  */
   uint32_t out_size;       /* FC: number of outputs; Poisson: = in_size      */
   uint32_t cin, h, w, cout, kh, kw, stride, pad; /* conv geometry          */
+  uint32_t log2_p;         /* the layer's message space p_l = 2^log2_p (DiNN's
+                              dynamic message space, 5.2); 0: the key's.  The
+                              layer's currents, membranes and bootstrap boxes
+                              live in Z_{2 p_l}; its spikes are written in the
+                              space of the next layer (the key's for the last
+                              layer: the scores).  The first layer reads the
+                              input in the key's space: a WeightSum first layer
+                              needs p_0 <= p (its weights are applied times
+                              p / p_0), a Poisson layer p_0 = p.  Other spaces
+                              than the key's need FHE_LIF_MULTI_VALUE and at
+                              most FHE_LUT_MAX_GROUPS layers.                 */
 } fhe_layer_desc;
 
 typedef struct fhe_snn_desc {
@@ -287,7 +326,8 @@ typedef struct fhe_snn_desc {
 /* Build a network on `keys` (uploads weights, allocates state for
  * max_images images; synchronous).  Errors: FHE_EINVAL (bad geometry, a
  * Poisson layer that is not the first or without static input, an unknown
- * lif_mode, FHE_LIF_TWO_PBS with spike_scale != 2), FHE_ENOMEM. */
+ * lif_mode, FHE_LIF_TWO_PBS with spike_scale != 2, a layer message space
+ * that breaks the rules of fhe_layer_desc.log2_p), FHE_ENOMEM. */
 int fhe_snn_create(fhe_keys *keys, const fhe_snn_desc *desc, fhe_snn **out);
 void fhe_snn_free(fhe_snn *net);
 

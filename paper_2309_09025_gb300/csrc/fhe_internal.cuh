@@ -143,15 +143,61 @@ struct fhe_keys {
   unsigned long long *d_fft_maxerr;
 };
 
+namespace fhe {
+// Table groups of one multi-value table set (one per layer of a network
+// whose layers have their own message spaces).
+constexpr uint32_t kLutGroups = FHE_LUT_MAX_GROUPS;
+}  // namespace fhe
+
 struct fhe_lut {
   uint32_t L;
   uint32_t N;
+  uint32_t groups;       // table groups (more than one only when L == 2)
   uint32_t *d_tv;        // L == 1: test polynomial [N]
-  int32_t *d_rpos;       // L == 2: sparse (1 - X) * coeffs(f_j): positions
-  int32_t *d_rval;       //         and values, concatenated for j = 0, 1
-  uint32_t nnz[2];
-  uint32_t off[2];
+  int32_t *d_rpos;       // L == 2: sparse (Delta_j / Delta_min) (1 - X) coeffs(f_j):
+  int32_t *d_rval;       //         positions and values, concatenated per group and j
+  uint32_t tv0[fhe::kLutGroups];     // L == 2: TV0 coefficient of each group (Delta_min / 2)
+  uint32_t nnz[fhe::kLutGroups][2];
+  uint32_t off[fhe::kLutGroups][2];
 };
+
+namespace fhe {
+// The tables of one bootstrap launch as its kernel reads them (a by-value
+// kernel parameter).  L = 1: the test polynomial tv.  L = 2 (multi-value):
+// group g rotates TV0 = tv0[g] * sum_i X^i and applies r_{g,j}, the entries
+// [off[g][j], off[g][j] + nnz[g][j]) of rpos / rval; ciphertext i of the
+// launch belongs to group g = #{q : i >= seg_end[q]}.
+struct LutArgs {
+  uint32_t L;
+  const uint32_t *tv;
+  const int32_t *rpos;
+  const int32_t *rval;
+  uint64_t seg_end[kLutGroups - 1];
+  uint32_t tv0[kLutGroups];
+  uint32_t off[kLutGroups][2];
+  uint32_t nnz[kLutGroups][2];
+};
+
+struct LutGroup {
+  uint32_t tv0, off0, nnz0, off1, nnz1;
+};
+
+// Group of ciphertext i; only compile-time indices into the parameter.
+__device__ __forceinline__ LutGroup lut_group(const LutArgs &a, uint64_t i) {
+  uint32_t g = 0;
+#pragma unroll
+  for (uint32_t q = 0; q + 1u < kLutGroups; ++q) g += (i >= a.seg_end[q]) ? 1u : 0u;
+  LutGroup s = {a.tv0[0], a.off[0][0], a.nnz[0][0], a.off[0][1], a.nnz[0][1]};
+#pragma unroll
+  for (uint32_t q = 1; q < kLutGroups; ++q)
+    if (g == q) s = LutGroup{a.tv0[q], a.off[q][0], a.nnz[q][0], a.off[q][1], a.nnz[q][1]};
+  return s;
+}
+
+// Kernel view of `lut` for the ciphertexts [s0, ...) of a call whose group
+// boundaries are seg_end (groups - 1 call-relative ends; NULL: one group).
+LutArgs lut_args(const fhe_lut *lut, const uint64_t *seg_end, uint64_t s0);
+}  // namespace fhe
 
 // On failure, also clear the runtime's last-error slot so that a
 // recoverable error does not resurface in later, unrelated checks.
@@ -170,16 +216,21 @@ void note_launches(int64_t n);
 uint64_t launches();
 // Implemented in fhe_pbs_exact.cu / fhe_pbs_tc.cu.
 // Table j of the outputs starts at ct_out + j * table_stride (words).
+// seg_end: the group boundaries of a grouped table set (see lut_args).
 int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-              uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+              uint32_t *ct_out, size_t table_stride, cudaStream_t st,
+              const uint64_t *seg_end = nullptr);
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-           uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+           uint32_t *ct_out, size_t table_stride, cudaStream_t st,
+           const uint64_t *seg_end = nullptr);
 int pbs_fft(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-            uint32_t *ct_out, size_t table_stride, cudaStream_t st);
+            uint32_t *ct_out, size_t table_stride, cudaStream_t st,
+            const uint64_t *seg_end = nullptr);
 int fft_prepare(fhe_keys *K);
 // Dispatch on the variant (FHE_EINVAL for an unknown one).
 int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st);
+            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st,
+            const uint64_t *seg_end = nullptr);
 // Exact bootstrapping with the extracted ciphertexts in a caller buffer
 // (fhe_noalloc.cu); single batch, no allocation.
 int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,

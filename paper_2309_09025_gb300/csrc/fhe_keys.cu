@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <vector>
 
@@ -279,11 +280,12 @@ extern "C" int fhe_status(fhe_keys *K, void *stream) {
   return h ? FHE_ETIMEOUT : FHE_OK;
 }
 
-// Test polynomial coefficients (centred boxes): coeff[c] = f[round(c p / N)]
-// for boxes below p, -f[0] on the wrapped half box (Thm 2.1's negacyclic
-// condition with one padding bit).
-static void lut_coefficients(const Params &P, const int32_t *f, std::vector<int32_t> &co) {
-  const uint32_t N = P.N, p = P.p();
+// Test polynomial coefficients (centred boxes) for the message space
+// p = 2^log2_p: coeff[c] = f[round(c p / N)] for boxes below p, -f[0] on the
+// wrapped half box (Thm 2.1's negacyclic condition with one padding bit).
+static void lut_coefficients(uint32_t N, uint32_t log2_p, const int32_t *f,
+                             std::vector<int32_t> &co) {
+  const uint32_t p = 1u << log2_p;
   co.resize(N);
   for (uint32_t c = 0; c < N; ++c) {
     uint32_t u = (c * p + N / 2u) / N;
@@ -291,35 +293,62 @@ static void lut_coefficients(const Params &P, const int32_t *f, std::vector<int3
   }
 }
 
-extern "C" int fhe_lut_create(const fhe_keys *K, const int32_t *f, uint32_t L, fhe_lut **out) {
-  if (!K || !f || !out || (L != 1u && L != 2u)) return FHE_EINVAL;
-  *out = NULL;
+// A bootstrap may read its input in one message space and write each table
+// in another (the dynamic message space of DiNN, adopted by the paper in
+// 5.2): boxes of p_in = 2^log2_p_in, outputs encoded with
+// Delta_j = 2^(31 - log2_p_out[j]).  Multi-value groups rotate
+// TV0 = (Delta_min / 2) sum X^i (Delta_min: the group's smallest Delta) and
+// apply r_j = (Delta_j / Delta_min) (1 - X) coeffs(f_j), so that
+// r_j * TV0 = Delta_j coeffs(f_j) mod X^N + 1.
+extern "C" int fhe_lut_create_spaces(const fhe_keys *K, const int32_t *f, uint32_t L,
+                                     uint32_t groups, const uint32_t *log2_p_in,
+                                     const uint32_t *log2_p_out, fhe_lut **out) {
+  if (!K || !f || !out || !log2_p_in || !log2_p_out || (L != 1u && L != 2u) || groups < 1u ||
+      groups > fhe::kLutGroups || (L == 1u && groups != 1u))
+    return FHE_EINVAL;
   const Params &P = K->P;
+  for (uint32_t g = 0; g < groups; ++g) {
+    if (log2_p_in[g] < 1u || log2_p_in[g] > 10u || (2u << log2_p_in[g]) > P.N) return FHE_EINVAL;
+    for (uint32_t j = 0; j < L; ++j)
+      if (log2_p_out[g * L + j] < 1u || log2_p_out[g * L + j] > 10u) return FHE_EINVAL;
+  }
+  *out = NULL;
   fhe_lut *T = (fhe_lut *)calloc(1, sizeof(fhe_lut));
   if (!T) return FHE_ENOMEM;
   T->L = L;
   T->N = P.N;
+  T->groups = groups;
   std::vector<int32_t> co;
   if (L == 1u) {
-    lut_coefficients(P, f, co);
+    lut_coefficients(P.N, log2_p_in[0], f, co);
+    const uint32_t delta_out = 1u << (31u - log2_p_out[0]);
     std::vector<uint32_t> tv(P.N);
-    for (uint32_t c = 0; c < P.N; ++c) tv[c] = (uint32_t)co[c] * P.delta();
+    for (uint32_t c = 0; c < P.N; ++c) tv[c] = (uint32_t)co[c] * delta_out;
     if (cudaMalloc(&T->d_tv, sizeof(uint32_t) * P.N) != cudaSuccess) { free(T); return FHE_ENOMEM; }
     if (cudaMemcpy(T->d_tv, tv.data(), sizeof(uint32_t) * P.N, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(T->d_tv); free(T); return FHE_ECUDA;
     }
   } else {
-    // r_j = (1 - X) * coeffs(f_j) mod X^N + 1, kept sparse (the table's jumps)
+    // r_{g,j}, kept sparse (the table's jumps); tables of group g start at
+    // f + sum_{h<g} 2 p_h
     std::vector<int32_t> pos, val;
-    for (uint32_t j = 0; j < 2u; ++j) {
-      lut_coefficients(P, f + (size_t)j * P.p(), co);
-      T->off[j] = (uint32_t)pos.size();
-      for (uint32_t c = 0; c < P.N; ++c) {
-        uint32_t r = (c == 0) ? (uint32_t)co[0] + (uint32_t)co[P.N - 1u]
-                              : (uint32_t)co[c] - (uint32_t)co[c - 1u];
-        if (r) { pos.push_back((int32_t)c); val.push_back((int32_t)r); }
+    const int32_t *fg = f;
+    for (uint32_t g = 0; g < groups; ++g) {
+      const uint32_t p = 1u << log2_p_in[g];
+      const uint32_t lp_max = std::max(log2_p_out[2u * g], log2_p_out[2u * g + 1u]);
+      T->tv0[g] = 1u << (30u - lp_max);
+      for (uint32_t j = 0; j < 2u; ++j) {
+        const uint32_t scale = 1u << (lp_max - log2_p_out[2u * g + j]);
+        lut_coefficients(P.N, log2_p_in[g], fg + (size_t)j * p, co);
+        T->off[g][j] = (uint32_t)pos.size();
+        for (uint32_t c = 0; c < P.N; ++c) {
+          const uint32_t r = scale * ((c == 0) ? (uint32_t)co[0] + (uint32_t)co[P.N - 1u]
+                                               : (uint32_t)co[c] - (uint32_t)co[c - 1u]);
+          if (r) { pos.push_back((int32_t)c); val.push_back((int32_t)r); }
+        }
+        T->nnz[g][j] = (uint32_t)pos.size() - T->off[g][j];
       }
-      T->nnz[j] = (uint32_t)pos.size() - T->off[j];
+      fg += 2u * (size_t)p;
     }
     size_t bytes = sizeof(int32_t) * (pos.size() ? pos.size() : 1u);
     if (cudaMalloc(&T->d_rpos, bytes) != cudaSuccess || cudaMalloc(&T->d_rval, bytes) != cudaSuccess) {
@@ -334,6 +363,36 @@ extern "C" int fhe_lut_create(const fhe_keys *K, const int32_t *f, uint32_t L, f
   *out = T;
   return FHE_OK;
 }
+
+extern "C" int fhe_lut_create(const fhe_keys *K, const int32_t *f, uint32_t L, fhe_lut **out) {
+  if (!K) return FHE_EINVAL;
+  const uint32_t lp[2] = {K->P.log2_p, K->P.log2_p};
+  return fhe_lut_create_spaces(K, f, L, 1u, lp, lp, out);
+}
+
+namespace fhe {
+LutArgs lut_args(const fhe_lut *T, const uint64_t *seg_end, uint64_t s0) {
+  LutArgs a;
+  memset(&a, 0, sizeof(a));
+  a.L = T->L;
+  a.tv = T->d_tv;
+  a.rpos = T->d_rpos;
+  a.rval = T->d_rval;
+  for (uint32_t q = 0; q + 1u < kLutGroups; ++q) {
+    uint64_t e = UINT64_MAX;  // past every ciphertext: groups above q + 1 unused
+    if (seg_end && q + 1u < T->groups) e = (seg_end[q] > s0) ? seg_end[q] - s0 : 0u;
+    a.seg_end[q] = e;
+  }
+  for (uint32_t g = 0; g < kLutGroups; ++g) {
+    a.tv0[g] = T->tv0[g];
+    for (uint32_t j = 0; j < 2u; ++j) {
+      a.off[g][j] = T->off[g][j];
+      a.nnz[g][j] = T->nnz[g][j];
+    }
+  }
+  return a;
+}
+}  // namespace fhe
 
 extern "C" void fhe_lut_free(fhe_lut *T) {
   if (!T) return;

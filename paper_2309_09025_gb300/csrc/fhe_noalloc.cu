@@ -42,7 +42,8 @@ int scratch_for_current_device(uint32_t **out) {
 
 extern "C" int fhe_pbs_batch_noalloc(const fhe_keys *K, const uint32_t *ct_in, size_t count,
                                      const fhe_lut *lut, uint32_t *ct_out, void *stream) {
-  if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N) return FHE_EINVAL;
+  if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N || lut->groups != 1u)
+    return FHE_EINVAL;
   if (!count) return FHE_OK;
   const uint64_t words = (uint64_t)lut->L * count * K->P.big_words();
   if (words > (uint64_t)FHE_PBS_NOALLOC_MAX_WORDS) return FHE_EINVAL;

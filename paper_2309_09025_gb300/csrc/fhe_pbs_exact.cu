@@ -21,6 +21,7 @@
 
 #include "fhe_internal.cuh"
 
+using fhe::LutArgs;
 using fhe::Params;
 
 namespace {
@@ -91,14 +92,6 @@ __global__ void k_selftest_timeout(uint64_t limit_ns, int *status) {
   }
 }
 
-struct LutArgs {
-  uint32_t L;
-  const uint32_t *tv;
-  const int32_t *rpos;
-  const int32_t *rval;
-  uint32_t nnz0, nnz1, off0, off1;
-};
-
 // Unpack 8 int16 (one 16-byte load) into int32.
 __device__ __forceinline__ void unpack8(const int16_t *src, int32_t *dst) {
   uint4 v = *reinterpret_cast<const uint4 *>(src);
@@ -129,8 +122,9 @@ __host__ __device__ inline BrSmem br_smem(uint32_t N, uint32_t CPC, uint32_t R, 
 template <int N, int CPC>
 __global__ void __launch_bounds__((N / 8) * (CPC / 2))
     k_blind_rotate_exact(Params P, const uint32_t *__restrict__ bsk,
-                         const uint32_t *__restrict__ ct_in, size_t count, LutArgs lut,
-                         uint32_t *__restrict__ big_out, int *status) {
+                         const uint32_t *__restrict__ ct_in, size_t count,
+                         const __grid_constant__ LutArgs lut, uint32_t *__restrict__ big_out,
+                         int *status) {
   constexpr int THREADS = (N / 8) * (CPC / 2);
   constexpr uint32_t LOG2_2N = (N == 256) ? 9 : (N == 512) ? 10 : (N == 1024) ? 11 : 12;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -159,15 +153,19 @@ __global__ void __launch_bounds__((N / 8) * (CPC / 2))
     abar_s[e] = (uint16_t)fhe::mod_switch_2n(v, LOG2_2N);
   }
   __syncthreads();
-  // ACC = (0, X^{-b~} TV); the multi-value case rotates the constant Delta/2
-  const uint32_t half_delta = P.delta() >> 1;
+  // ACC = (0, X^{-b~} TV); the multi-value case rotates the constant TV0
+  // coefficient of the ciphertext's table group
   for (uint32_t e = tid; e < CPC * N; e += THREADS) {
     uint32_t b = e / N, c = e % N;
     uint32_t bb = abar_s[b * (n + 1u) + n];
     uint32_t s = (c + bb) & (2u * N - 1u);
     uint32_t v;
-    if (lut.L == 1u) v = (s < N) ? lut.tv[s] : (0u - lut.tv[s - N]);
-    else v = (s < N) ? half_delta : (0u - half_delta);
+    if (lut.L == 1u) {
+      v = (s < N) ? lut.tv[s] : (0u - lut.tv[s - N]);
+    } else {
+      const uint32_t tv0 = fhe::lut_group(lut, base + b).tv0;
+      v = (s < N) ? tv0 : (0u - tv0);
+    }
     acc_s[(b * 2u + 0u) * N + c] = 0u;
     acc_s[(b * 2u + 1u) * N + c] = v;
   }
@@ -278,10 +276,11 @@ __global__ void __launch_bounds__((N / 8) * (CPC / 2))
   // a'_0 = A[0], a'_c = -A[N - c], b' = B[0].
   const uint32_t W = N + 1u;
   for (uint32_t j = 0; j < lut.L; ++j) {
-    const uint32_t nnz = j ? lut.nnz1 : lut.nnz0, off = j ? lut.off1 : lut.off0;
     for (uint32_t e = tid; e < CPC * W; e += THREADS) {
       const uint32_t b = e / W, c = e % W;
       if (base + b >= count) continue;
+      const fhe::LutGroup grp = fhe::lut_group(lut, base + b);
+      const uint32_t nnz = j ? grp.nnz1 : grp.nnz0, off = j ? grp.off1 : grp.off0;
       const uint32_t *A = acc_s + (b * 2u) * N;
       const uint32_t *B = acc_s + (b * 2u + 1u) * N;
       uint32_t v;
@@ -413,17 +412,11 @@ int key_switch_batch(const fhe_keys *K, const uint32_t *d_big, size_t count, uin
 }
 
 int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-              uint32_t *ct_out, size_t table_stride, cudaStream_t st) {
+              uint32_t *ct_out, size_t table_stride, cudaStream_t st, const uint64_t *seg_end) {
   const Params &P = K->P;
-  LutArgs la;
-  la.L = lut->L;
-  la.tv = lut->d_tv;
-  la.rpos = lut->d_rpos;
-  la.rval = lut->d_rval;
-  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
-  la.off0 = lut->off[0]; la.off1 = lut->off[1];
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
+    const LutArgs la = lut_args(lut, seg_end, s0);
     const uint32_t *in = ct_in + s0 * (P.n + 1u);
     int rc;
     const bool prof = (s0 == 0) && K->prof_ev0;
@@ -452,13 +445,7 @@ int pbs_exact(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *l
 int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                    uint32_t *ct_out, uint32_t *big, cudaStream_t st) {
   const Params &P = K->P;
-  LutArgs la;
-  la.L = lut->L;
-  la.tv = lut->d_tv;
-  la.rpos = lut->d_rpos;
-  la.rval = lut->d_rval;
-  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
-  la.off0 = lut->off[0]; la.off1 = lut->off[1];
+  const LutArgs la = lut_args(lut, nullptr, 0);
   int rc;
   switch (P.N) {
     case 256: rc = launch_br<256, 8>(K, ct_in, count, la, big, st); break;
@@ -477,13 +464,16 @@ int pbs_exact_into(const fhe_keys *K, const uint32_t *ct_in, size_t count, const
 }
 
 int pbs_run(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st) {
+            uint32_t *ct_out, size_t table_stride, int variant, cudaStream_t st,
+            const uint64_t *seg_end) {
   if (!count) return FHE_OK;
   if (variant == FHE_VARIANT_AUTO)  // both exact paths give the same bits
     variant = (count >= K->tc_min_batch) ? FHE_VARIANT_TC : FHE_VARIANT_EXACT;
-  if (variant == FHE_VARIANT_EXACT) return pbs_exact(K, ct_in, count, lut, ct_out, table_stride, st);
-  if (variant == FHE_VARIANT_TC) return pbs_tc(K, ct_in, count, lut, ct_out, table_stride, st);
-  if (variant == FHE_VARIANT_FFT) return pbs_fft(K, ct_in, count, lut, ct_out, table_stride, st);
+  if (variant == FHE_VARIANT_EXACT)
+    return pbs_exact(K, ct_in, count, lut, ct_out, table_stride, st, seg_end);
+  if (variant == FHE_VARIANT_TC) return pbs_tc(K, ct_in, count, lut, ct_out, table_stride, st, seg_end);
+  if (variant == FHE_VARIANT_FFT)
+    return pbs_fft(K, ct_in, count, lut, ct_out, table_stride, st, seg_end);
   return FHE_EINVAL;
 }
 
@@ -500,8 +490,26 @@ extern "C" int fhe_selftest_timeout(fhe_keys *K, uint32_t limit_us, void *stream
 
 extern "C" int fhe_pbs_batch(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                              uint32_t *ct_out, int variant, void *stream) {
-  if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N) return FHE_EINVAL;
+  if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N || lut->groups != 1u)
+    return FHE_EINVAL;
   if (!count) return FHE_OK;
   cudaStream_t st = (cudaStream_t)stream;
   return fhe::pbs_run(K, ct_in, count, lut, ct_out, count * (K->P.n + 1u), variant, st);
+}
+
+extern "C" int fhe_pbs_batch_groups(fhe_keys *K, const uint32_t *ct_in, size_t count,
+                                    const fhe_lut *lut, const size_t *seg_end, uint32_t *ct_out,
+                                    int variant, void *stream) {
+  if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N ||
+      (lut->groups > 1u && !seg_end))
+    return FHE_EINVAL;
+  uint64_t ends[fhe::kLutGroups - 1];
+  for (uint32_t q = 0; q + 1u < lut->groups; ++q) {
+    if (seg_end[q] > count || (q && seg_end[q] < seg_end[q - 1])) return FHE_EINVAL;
+    ends[q] = seg_end[q];
+  }
+  if (!count) return FHE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return fhe::pbs_run(K, ct_in, count, lut, ct_out, count * (K->P.n + 1u), variant, st,
+                      lut->groups > 1u ? ends : nullptr);
 }

@@ -22,6 +22,7 @@
 
 #include "fhe_internal.cuh"
 
+using fhe::LutArgs;
 using fhe::Params;
 
 namespace {
@@ -63,14 +64,6 @@ __device__ __forceinline__ int bitrev(int k) {
   return (int)(__brev((unsigned)k) >> (32 - LOGM));
 }
 
-struct FftLut {
-  uint32_t L;
-  const uint32_t *tv;
-  const int32_t *rpos;
-  const int32_t *rval;
-  uint32_t nnz0, nnz1, off0, off1;
-};
-
 // Key spectra: for every GGSW polynomial (i, row, comp) the transform of its
 // words read as signed 32-bit integers.  One CTA per polynomial.
 template <int M>
@@ -92,7 +85,8 @@ template <int N>
 __global__ void __launch_bounds__(kFftThreads)
     k_blind_rotate_fft(Params P, const double2 *__restrict__ kspec, const double2 *__restrict__ twist,
                        const double2 *__restrict__ tw, const uint32_t *__restrict__ ct_in,
-                       size_t count, FftLut lut, uint32_t *__restrict__ big_out,
+                       size_t count, const __grid_constant__ LutArgs lut,
+                       uint32_t *__restrict__ big_out,
                        unsigned long long *max_err_bits) {
   constexpr int M = N / 2;
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
@@ -104,16 +98,17 @@ __global__ void __launch_bounds__(kFftThreads)
   const uint32_t *ct = ct_in + cti * (n + 1u);
   const uint32_t total_bits = l * P.log2_bg;
   const uint32_t Bmask = (1u << P.log2_bg) - 1u, Bhalf = 1u << (P.log2_bg - 1u);
-  const uint32_t half_delta = P.delta() >> 1;
   const double inv_m = 1.0 / (double)M;
   double max_err = 0.0;
 
+  // the table group of this CTA's ciphertext (multi-value: TV0 and r_j)
+  const fhe::LutGroup grp = fhe::lut_group(lut, cti);
   const uint32_t bb = fhe::mod_switch_2n(ct[n], LOG2_2N);
   for (uint32_t c = threadIdx.x; c < (uint32_t)N; c += kFftThreads) {
     const uint32_t s = (c + bb) & (2u * N - 1u);
     uint32_t v;
     if (lut.L == 1u) v = (s < (uint32_t)N) ? lut.tv[s] : (0u - lut.tv[s - N]);
-    else v = (s < (uint32_t)N) ? half_delta : (0u - half_delta);
+    else v = (s < (uint32_t)N) ? grp.tv0 : (0u - grp.tv0);
     acc[c] = 0u;
     acc[N + c] = v;
   }
@@ -196,7 +191,7 @@ __global__ void __launch_bounds__(kFftThreads)
   // sample extraction (multi-value split when L == 2)
   const uint32_t W = N + 1u;
   for (uint32_t jl = 0; jl < lut.L; ++jl) {
-    const uint32_t nnz = jl ? lut.nnz1 : lut.nnz0, off = jl ? lut.off1 : lut.off0;
+    const uint32_t nnz = jl ? grp.nnz1 : grp.nnz0, off = jl ? grp.off1 : grp.off0;
     for (uint32_t c = threadIdx.x; c < W; c += kFftThreads) {
       const uint32_t *A = acc, *B = acc + N;
       uint32_t v;
@@ -261,22 +256,16 @@ int fft_prepare(fhe_keys *K) {
 }
 
 int pbs_fft(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-            uint32_t *ct_out, size_t table_stride, cudaStream_t st) {
+            uint32_t *ct_out, size_t table_stride, cudaStream_t st, const uint64_t *seg_end) {
   const Params &P = K->P;
   if (!fft_supported(P)) return FHE_EUNSUPPORTED;
   int rc = fft_prepare(K);
   if (rc) return rc;
-  FftLut la;
-  la.L = lut->L;
-  la.tv = lut->d_tv;
-  la.rpos = lut->d_rpos;
-  la.rval = lut->d_rval;
-  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
-  la.off0 = lut->off[0]; la.off1 = lut->off[1];
   const uint32_t M = P.N / 2u, R = P.rows();
   const size_t smem = (size_t)R * M * 16u + 2u * P.N * 4u;
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
+    const LutArgs la = lut_args(lut, seg_end, s0);
     const bool prof = (s0 == 0) && K->prof_ev0;
     if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
     if (P.N == 1024u) {

@@ -51,6 +51,7 @@
 
 #include "fhe_internal.cuh"
 
+using fhe::LutArgs;
 using fhe::Params;
 
 namespace {
@@ -250,14 +251,6 @@ __global__ void k_hankel_strips(Params P, const uint32_t *__restrict__ bsk, __ha
   }
 }
 
-struct TcLut {
-  uint32_t L;
-  const uint32_t *tv;
-  const int32_t *rpos;
-  const int32_t *rval;
-  uint32_t nnz0, nnz1, off0, off1;
-};
-
 struct TcSmem {
   uint32_t a, b, bars, tmem_slot, total;
 };
@@ -288,7 +281,8 @@ __host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) 
 template <int N, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
-                      const uint32_t *__restrict__ ct_in, size_t count, TcLut lut,
+                      const uint32_t *__restrict__ ct_in, size_t count,
+                      const __grid_constant__ LutArgs lut,
                       uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
                       uint32_t chunk_r, uint32_t sub_shift, uint32_t *__restrict__ big_out,
                       int *status) {
@@ -364,16 +358,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                  "r"((uint32_t)kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
-  // initial accumulators of this CTA's RPC ciphertexts: (0, X^{-b~} TV)
-  const uint32_t half_delta = P.delta() >> 1;
+  // initial accumulators of this CTA's RPC ciphertexts: (0, X^{-b~} TV);
+  // multi-value: the TV0 coefficient of the ciphertext's table group
   for (uint32_t e = tid; e < RPC * N; e += kThreads) {
     const uint32_t b = row0 + e / N, c = e % N;
     const uint32_t v_ct = (base + b < count) ? ct_in[(base + b) * (n + 1u) + n] : 0u;
     const uint32_t bb = fhe::mod_switch_2n(v_ct, LOG2_2N);
     const uint32_t s = (c + bb) & (2u * N - 1u);
     uint32_t v;
-    if (lut.L == 1u) v = (s < N) ? lut.tv[s] : (0u - lut.tv[s - N]);
-    else v = (s < N) ? half_delta : (0u - half_delta);
+    if (lut.L == 1u) {
+      v = (s < N) ? lut.tv[s] : (0u - lut.tv[s - N]);
+    } else {
+      const uint32_t tv0 = fhe::lut_group(lut, base + b).tv0;
+      v = (s < N) ? tv0 : (0u - tv0);
+    }
     acc[((uint64_t)b * 2u + 0u) * N + c] = 0u;
     acc[((uint64_t)b * 2u + 1u) * N + c] = v;
   }
@@ -701,10 +699,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   // ---- sample extraction (with the multi-value split when L == 2)
   const uint32_t W = N + 1u;
   for (uint32_t jl = 0; jl < lut.L; ++jl) {
-    const uint32_t nnz = jl ? lut.nnz1 : lut.nnz0, off = jl ? lut.off1 : lut.off0;
     for (uint32_t e = tid; e < RPC * W; e += kThreads) {
       const uint32_t b = row0 + e / W, c = e % W;
       if (base + b >= count) continue;
+      const fhe::LutGroup grp = fhe::lut_group(lut, base + b);
+      const uint32_t nnz = jl ? grp.nnz1 : grp.nnz0, off = jl ? grp.off1 : grp.off0;
       const uint32_t *A = acc + ((uint64_t)b * 2u) * N;
       const uint32_t *B = acc + ((uint64_t)b * 2u + 1u) * N;
       uint32_t v;
@@ -802,18 +801,11 @@ int pbs_prepare(fhe_keys *K, int variant) {
 }
 
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
-           uint32_t *ct_out, size_t table_stride, cudaStream_t st) {
+           uint32_t *ct_out, size_t table_stride, cudaStream_t st, const uint64_t *seg_end) {
   const Params &P = K->P;
   if (!tc_supported(P)) return FHE_EUNSUPPORTED;
   int rc = tc_prepare(K);
   if (rc) return rc;
-  TcLut la;
-  la.L = lut->L;
-  la.tv = lut->d_tv;
-  la.rpos = lut->d_rpos;
-  la.rval = lut->d_rval;
-  la.nnz0 = lut->nnz[0]; la.nnz1 = lut->nnz[1];
-  la.off0 = lut->off[0]; la.off1 = lut->off[1];
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem();
   auto kern4 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 4> : k_blind_rotate_tc<2048, 4>;
@@ -831,6 +823,7 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   }
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
+    const LutArgs la = lut_args(lut, seg_end, s0);
     const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
     // a batch that fits in one wave of 8-CTA clusters runs with half the work
     // per CTA and step (lower latency); larger ones use the 36 clusters of 4

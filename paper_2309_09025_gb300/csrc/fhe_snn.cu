@@ -33,6 +33,7 @@ int lwe_add_offsets(uint32_t n, const uint32_t *a, const int32_t *offs, uint32_t
 namespace {
 struct Layer {
   int type;
+  uint32_t log2_p;  // the layer's message space
   int32_t *d_w;   // weights; Poisson: thresholds M [T][in_size]
   uint32_t in_size, out_size;
   uint32_t cin, h, w, cout, kh, kw, stride, pad;
@@ -62,7 +63,9 @@ struct fhe_snn {
   fhe_snn_desc desc;
   std::vector<Layer> layers;
   int mode;               // FHE_LIF_MULTI_VALUE or FHE_LIF_TWO_PBS
-  fhe_lut *lut;           // multi-value: Fire and Reset tables (L = 2)
+  fhe_lut *lut;           // multi-value: Fire and Reset tables (L = 2), one
+                          // group per layer when the layers have their own
+                          // message spaces
   fhe_lut *lut_fire;      // two bootstraps: sign table (L = 1)
   fhe_lut *lut_reset;     // two bootstraps: reset table (L = 1)
   uint32_t n_in, n_out;
@@ -97,6 +100,12 @@ struct fhe_snn {
   std::vector<cudaEvent_t> ev;   // [iterations][2 launches][2]
   std::vector<size_t> ev_count;  // [iterations][2]: ciphertexts of each bracketed launch
 };
+
+// Centring offset (p_l / 2) * Delta_l of a layer's bootstrap input (q / 4
+// whatever the space).
+static uint32_t half_space(uint32_t log2_p) {
+  return (1u << (log2_p - 1u)) * (1u << (31u - log2_p));
+}
 
 static uint32_t snn_iterations(const fhe_snn *S) {
   return S->desc.T + (uint32_t)S->layers.size() - 1u;
@@ -154,6 +163,19 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   *out = NULL;
   const fhe::Params &P = K->P;
   const int32_t p = (int32_t)P.p();
+  // message spaces of the layers (DiNN's dynamic message space, 5.2)
+  const uint32_t nl = d->n_layers;
+  std::vector<uint32_t> lp(nl);
+  bool spaces = false;
+  for (uint32_t i = 0; i < nl; ++i) {
+    const fhe_layer_desc &ld = d->layers[i];
+    lp[i] = ld.log2_p ? ld.log2_p : P.log2_p;
+    if (lp[i] > 10u || (2u << lp[i]) > P.N) return FHE_EINVAL;
+    if (i == 0 && (lp[0] > P.log2_p || (ld.type == FHE_LAYER_POISSON && lp[0] != P.log2_p)))
+      return FHE_EINVAL;
+    spaces = spaces || lp[i] != P.log2_p;
+  }
+  if (spaces && (d->lif_mode != FHE_LIF_MULTI_VALUE || nl > fhe::kLutGroups)) return FHE_EINVAL;
   fhe_snn *S = new fhe_snn();
   S->K = K;
   S->desc = *d;
@@ -163,13 +185,26 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
   if (rc) { snn_release(S); return rc; }
   std::vector<int32_t> f(2u * (size_t)p);
   if (S->mode == FHE_LIF_MULTI_VALUE) {
-    // LIF tables on the centred input u = H + p/2, v = u - p/2 (Thm 3.2 / 4.2)
-    for (int32_t u = 0; u < p; ++u) {
-      const int32_t v = u - p / 2;
-      f[u] = (v >= d->v_th) ? d->spike_scale : 0;
-      f[p + u] = (v >= d->v_th) ? 0 : (v >= 0 ? (v >> d->leak_shift) : 0);
+    // LIF tables on the centred input u = H + p_l/2, v = u - p_l/2 (Thm 3.2 /
+    // 4.2); one group per layer when the spaces differ: Fire written in the
+    // next layer's space (the key's after the last layer), Reset in its own
+    const uint32_t groups = spaces ? nl : 1u;
+    std::vector<uint32_t> lp_in(groups), lp_out(2u * groups);
+    f.clear();
+    for (uint32_t g = 0; g < groups; ++g) {
+      lp_in[g] = lp[g];
+      lp_out[2u * g] = (g + 1u < groups) ? lp[g + 1u] : P.log2_p;
+      lp_out[2u * g + 1u] = lp[g];
+      const int32_t pg = 1 << lp[g];
+      const size_t at = f.size();
+      f.resize(at + 2u * (size_t)pg);
+      for (int32_t u = 0; u < pg; ++u) {
+        const int32_t v = u - pg / 2;
+        f[at + u] = (v >= d->v_th) ? d->spike_scale : 0;
+        f[at + pg + u] = (v >= d->v_th) ? 0 : (v >= 0 ? (v >> d->leak_shift) : 0);
+      }
     }
-    rc = fhe_lut_create(K, f.data(), 2u, &S->lut);
+    rc = fhe_lut_create_spaces(K, f.data(), 2u, groups, lp_in.data(), lp_out.data(), &S->lut);
   } else {
     // Negacyclic program functions on u in [0, p) (4.2); the bootstrap gives
     // -g(u) on the other half [-p, 0).  Sign: g = 1.  Reset: 0 from V_th up,
@@ -189,6 +224,7 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
     Layer L;
     memset(&L, 0, sizeof(L));
     L.type = ld.type;
+    L.log2_p = lp[i];
     size_t wcount;
     if (ld.type == FHE_LAYER_FC) {
       L.in_size = ld.in_size; L.out_size = ld.out_size;
@@ -222,7 +258,16 @@ extern "C" int fhe_snn_create(fhe_keys *K, const fhe_snn_desc *d, fhe_snn **out)
                cudaMalloc(&L.d_I, sizeof(uint32_t) * cts * W) == cudaSuccess);
     S->layers.push_back(L);
     if (!ok) { snn_release(S); return FHE_ENOMEM; }
-    if (cudaMemcpy(L.d_w, ld.weights, sizeof(int32_t) * wcount, cudaMemcpyHostToDevice) != cudaSuccess) {
+    // a WeightSum first layer in a smaller space than the input's: the
+    // input's Delta times p / p_0 is the layer's
+    std::vector<int32_t> scaled;
+    const int32_t *wsrc = ld.weights;
+    if (i == 0 && L.type != FHE_LAYER_POISSON && lp[0] != P.log2_p) {
+      scaled.assign(ld.weights, ld.weights + wcount);
+      for (auto &w : scaled) w = (int32_t)((uint32_t)w << (P.log2_p - lp[0]));
+      wsrc = scaled.data();
+    }
+    if (cudaMemcpy(L.d_w, wsrc, sizeof(int32_t) * wcount, cudaMemcpyHostToDevice) != cudaSuccess) {
       snn_release(S); return FHE_ECUDA;
     }
   }
@@ -307,9 +352,10 @@ extern "C" int fhe_snn_profile(const fhe_snn *S, double *br_ms, uint64_t *br_lau
 
 // Bootstrap the ciphertexts [lo, hi) of `in` with `lut` into `out` (table
 // stride `stride`), bracketed by profiling slot `slot` of iteration tau.
+// seg_end: the launch-relative layer boundaries of a grouped table set.
 static int snn_bootstrap(fhe_snn *S, uint32_t tau, uint32_t slot, const uint32_t *in, size_t lo,
                          size_t hi, const fhe_lut *lut, uint32_t *out, size_t stride,
-                         cudaStream_t st) {
+                         cudaStream_t st, const uint64_t *seg_end = nullptr) {
   const uint32_t W = S->K->P.n + 1u;
   if (hi <= lo) return FHE_OK;
   const size_t e = 2u * tau + slot;
@@ -318,7 +364,7 @@ static int snn_bootstrap(fhe_snn *S, uint32_t tau, uint32_t slot, const uint32_t
     S->K->prof_ev1 = S->ev[2u * e + 1u];
   }
   const int rc = fhe::pbs_run(S->K, in + lo * W, hi - lo, lut, out + lo * W, stride,
-                              S->desc.variant, st);
+                              S->desc.variant, st, seg_end);
   if (S->profile) {
     S->ev_count[e] = S->K->prof_count;
     S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
@@ -378,7 +424,7 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
       if (rc) return rc;
       continue;
     }
-    rc = fhe::lwe_add(P.n, L.d_I, t ? mem + off[l] * W : NULL, two ? 0u : half_p, cnt,
+    rc = fhe::lwe_add(P.n, L.d_I, t ? mem + off[l] * W : NULL, two ? 0u : half_space(L.log2_p), cnt,
                       S->d_H + off[l] * W, st);
     if (!rc && two)
       rc = fhe::lwe_add(P.n, S->d_H + off[l] * W, NULL, 0u - (uint32_t)S->desc.v_th * delta, cnt,
@@ -387,7 +433,10 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
   }
   // 3. bootstraps for every active neuron: spikes and V in place
   if (!two) {
-    rc = snn_bootstrap(S, tau, 0u, S->d_H, off[lo], off[hi + 1], S->lut, spk, all * W, st);
+    std::vector<uint64_t> seg(nl, 0);  // layer boundaries relative to off[lo]
+    for (uint32_t q = 0; q + 1u < nl; ++q) seg[q] = (off[q + 1] > off[lo]) ? off[q + 1] - off[lo] : 0u;
+    rc = snn_bootstrap(S, tau, 0u, S->d_H, off[lo], off[hi + 1], S->lut, spk, all * W, st,
+                       S->lut->groups > 1u ? seg.data() : nullptr);
     if (rc) return rc;
   } else {
     rc = snn_bootstrap(S, tau, 0u, S->d_Hf, off[lo], off[hi + 1], S->lut_fire, spk, all * W, st);
@@ -574,7 +623,8 @@ static int stream_alloc(fhe_snn *S) {
 }
 
 static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi, const fhe_lut *lut,
-                            uint32_t *out, size_t stride, cudaStream_t st) {
+                            uint32_t *out, size_t stride, cudaStream_t st,
+                            const uint64_t *seg_end = nullptr) {
   if (hi <= lo) return FHE_OK;
   StreamState &Z = *S->stream;
   const uint32_t W = S->K->P.n + 1u;
@@ -590,7 +640,8 @@ static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi
     S->K->prof_ev0 = Z.ev[2u * Z.ev_used];
     S->K->prof_ev1 = Z.ev[2u * Z.ev_used + 1u];
   }
-  const int rc = fhe::pbs_run(S->K, in + lo * W, hi - lo, lut, out + lo * W, stride, S->desc.variant, st);
+  const int rc = fhe::pbs_run(S->K, in + lo * W, hi - lo, lut, out + lo * W, stride, S->desc.variant, st,
+                              seg_end);
   if (S->profile) {
     Z.ev_count[Z.ev_used++] = S->K->prof_count;
     S->K->prof_ev0 = S->K->prof_ev1 = (cudaEvent_t)0;
@@ -655,14 +706,18 @@ static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
       if (rc) return rc;
       continue;
     }
-    rc = fhe::lwe_add(P.n, Z.I[sl][l], t ? Z.mem[sl][l] : NULL, two ? 0u : half_p, cnt, h, st);
+    rc = fhe::lwe_add(P.n, Z.I[sl][l], t ? Z.mem[sl][l] : NULL, two ? 0u : half_space(L.log2_p), cnt,
+                      h, st);
     if (!rc && two) rc = fhe::lwe_add(P.n, h, NULL, 0u - (uint32_t)S->desc.v_th * delta, cnt, hf, st);
     if (rc) return rc;
   }
   // 3. one launch for every active neuron (two in the two-bootstrap mode)
   uint32_t *pout_v = Z.pout + all * W;
   if (!two) {
-    rc = stream_bootstrap(S, Z.stage_H, 0, off[nl], S->lut, Z.pout, all * W, st);
+    // layer boundaries of the gathered launch (inactive layers: empty)
+    const std::vector<uint64_t> seg(off.begin() + 1, off.end());
+    rc = stream_bootstrap(S, Z.stage_H, 0, off[nl], S->lut, Z.pout, all * W, st,
+                          S->lut->groups > 1u ? seg.data() : nullptr);
   } else {
     rc = stream_bootstrap(S, Z.stage_Hf, 0, off[nl], S->lut_fire, Z.pout, all * W, st);
     if (!rc) rc = fhe::lwe_add(P.n, Z.pout, NULL, delta, off[nl], Z.pout, st);

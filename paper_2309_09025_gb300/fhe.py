@@ -39,7 +39,9 @@ EXPORTED = (
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
     "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
+    "fhe_lut_create_spaces", "fhe_pbs_batch_groups",
 )
+LUT_MAX_GROUPS = 8
 PBS_NOALLOC_MAX_WORDS = 1 << 20
 
 
@@ -69,7 +71,8 @@ class LayerDesc(ctypes.Structure):
                 ("in_size", ctypes.c_uint32), ("out_size", ctypes.c_uint32),
                 ("cin", ctypes.c_uint32), ("h", ctypes.c_uint32), ("w", ctypes.c_uint32),
                 ("cout", ctypes.c_uint32), ("kh", ctypes.c_uint32), ("kw", ctypes.c_uint32),
-                ("stride", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("stride", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("log2_p", ctypes.c_uint32)]
 
 
 class SnnDesc(ctypes.Structure):
@@ -128,6 +131,8 @@ def lib():
             "fhe_snn_stream_push": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
             "fhe_snn_stream_flush": (ctypes.c_int, [vp, vp]),
             "fhe_pbs_autotune": (ctypes.c_int, [vp, ctypes.POINTER(u64), vp]),
+            "fhe_lut_create_spaces": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(vp)]),
+            "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -280,12 +285,32 @@ def lwe_conv2d(params, W, ct_in, cin, h, w, stride, pad, bias=None, batch=1, out
 
 
 class Lut:
-    def __init__(self, keys, f):
-        f = np.ascontiguousarray(np.asarray(f, np.int32).reshape(-1, 1 << keys.params["log2_p"]))
-        self.L = f.shape[0]
+    """Bootstrap tables (fhe_lut_create).  With log2_p_in / log2_p_out
+    (fhe_lut_create_spaces): f is a list of groups, group g an (L, 2^log2_p_in[g])
+    array whose table j is written in the space 2^log2_p_out[g][j]."""
+
+    def __init__(self, keys, f, log2_p_in=None, log2_p_out=None):
         h = ctypes.c_void_p()
-        _check(lib().fhe_lut_create(keys.handle, f.ctypes.data_as(ctypes.c_void_p), self.L,
-                                    ctypes.byref(h)), "lut_create")
+        if log2_p_in is None:
+            f = np.ascontiguousarray(np.asarray(f, np.int32).reshape(-1, 1 << keys.params["log2_p"]))
+            self.L = f.shape[0]
+            self.groups = 1
+            _check(lib().fhe_lut_create(keys.handle, f.ctypes.data_as(ctypes.c_void_p), self.L,
+                                        ctypes.byref(h)), "lut_create")
+        else:
+            lp_in = np.ascontiguousarray(np.asarray(log2_p_in, np.uint32).reshape(-1))
+            self.groups = lp_in.shape[0]
+            tabs = [np.asarray(fg, np.int32).reshape(-1, 1 << int(lp)) for fg, lp in zip(f, lp_in)]
+            self.L = tabs[0].shape[0]
+            flat = np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in tabs]))
+            lp_out = np.ascontiguousarray(np.asarray(log2_p_out, np.uint32).reshape(-1))
+            if len(tabs) != self.groups or lp_out.shape[0] != self.groups * self.L:
+                raise ValueError("one table group and L output spaces per input space")
+            _check(lib().fhe_lut_create_spaces(keys.handle, flat.ctypes.data_as(ctypes.c_void_p),
+                                               self.L, self.groups,
+                                               lp_in.ctypes.data_as(ctypes.c_void_p),
+                                               lp_out.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.byref(h)), "lut_create_spaces")
         self.handle = h
 
     def free(self):
@@ -317,6 +342,23 @@ def pbs_batch(keys, ct_in, lut, variant=VARIANT_EXACT, out=None, stream=None):
     return out
 
 
+def pbs_batch_groups(keys, ct_in, lut, seg_end, variant=VARIANT_EXACT, out=None, stream=None):
+    """fhe_pbs_batch_groups: inputs [seg_end[g-1], seg_end[g]) use table
+    group g of a grouped Lut; (L, count, n+1) int32."""
+    import torch
+    w = keys.params["n"] + 1
+    ct_in = _dev_u32(ct_in)
+    count = ct_in.numel() // w
+    if out is None:
+        out = torch.empty((lut.L, count, w), dtype=torch.int32, device="cuda")
+    ends = (ctypes.c_size_t * max(1, len(seg_end)))(*[int(e) for e in seg_end])
+    _check(lib().fhe_pbs_batch_groups(keys.handle, _ptr(ct_in), count, lut.handle,
+                                      ctypes.cast(ends, ctypes.c_void_p) if len(seg_end) else None,
+                                      _ptr(out), int(variant), _stream(stream)),
+           "pbs_batch_groups")
+    return out
+
+
 def pbs_batch_noalloc(keys, ct_in, lut, out=None, stream=None):
     """fhe_pbs_batch_noalloc: exact bootstrapping with the library's fixed
     scratch array (no allocation in the library); (L, count, n+1) int32."""
@@ -345,6 +387,7 @@ class Snn:
             self._weights.append(Wt)
             d = descs[i]
             d.weights = Wt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.log2_p = int(layer.get("log2_p", 0))
             if layer["type"] == "poisson":
                 d.type = LAYER_POISSON
                 d.in_size = d.out_size = Wt.shape[1]
