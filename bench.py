@@ -36,12 +36,10 @@ SM_COUNT = 152
 # INT32 multiply-add issue rate of one SM (4 SMSPs x 16 lanes per clock).
 IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one blind-rotation launch,
-# from the ncu captures summarised in profiles/blind_rotate_*_p630.md (the key
-# layout is read once per launch from DRAM, so the figure does not scale with
-# the batch).  Set to None whenever the kernel changes until re-captured.
-# DRAM bytes (read + write) per launch of the dominant kernel, from ncu
-# captures of the same launches (summaries under profiles/).
+# dram__bytes_read.sum + dram__bytes_write.sum of one blind-rotation launch
+# of the bench's own size, from the ncu captures summarised in
+# profiles/blind_rotate_*_p630.md.  Set to None whenever the kernel changes
+# until re-captured.
 TRAFFIC_BYTES = {"tc": (625840393984 + 121506430720 + 621329120000 + 121505306624) / 2,
                  "exact": 34.066688e6 + 16.64e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).

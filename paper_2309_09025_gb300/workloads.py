@@ -1,7 +1,7 @@
 """Streamed throughput of the network workloads (one JSON line each).
 
     python -m paper_2309_09025_gb300.workloads [--params P630] [--batches 3]
-                                               [--only csnn,csnn_two_pbs,paper_csnn,poisson]
+                                               [--only csnn,csnn_two_pbs,paper_csnn,poisson,csnn_spaces]
 
 Each workload runs on the tensor-core blind rotation through the streamed
 inference API (fhe_snn_stream_push): two warm-up batches fill the pipeline,
@@ -16,7 +16,10 @@ bootstrap launch holds about one wave of 36 clusters x 256 ciphertexts.
 * paper_csnn: conv 1->10 8x8 s2 pad 1 -> pooling folded into FC 1440->160
   -> FC 160->10, T = 2 (3.1, 3.3);
 * poisson: Poisson encoder of 784 pixels -> FC 784->160 -> FC 160->10,
-  T = 20 (2.3, Table Poisson).
+  T = 20 (2.3, Table Poisson);
+* csnn_spaces: the csnn network with per-layer message spaces p = 64, 32, 32
+  (DiNN's dynamic message space, 5.2): one grouped table set, every launch
+  still serving all active layers.
 """
 import argparse
 import json
@@ -32,7 +35,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--params", default="P630")
     ap.add_argument("--batches", type=int, default=3)
-    ap.add_argument("--only", default="csnn,csnn_two_pbs,paper_csnn,poisson")
+    ap.add_argument("--only", default="csnn,csnn_two_pbs,paper_csnn,poisson,csnn_spaces")
     ap.add_argument("--latency", action="store_true",
                     help="one image per call through fhe_snn_infer (graphs, AUTO variant): "
                          "latency of a single encrypted prediction")
@@ -44,11 +47,15 @@ def main():
     two["lif"] = dict(two["lif"], spike_scale=2)
     two["lif_mode"] = "two_pbs"  # spikes of value 2 stay inside Thm 4.1's doubled range
     px16 = lambda seed, n: synth.stroke_images(seed, n, levels=synth.POISSON_LEVELS)
+    spaced = synth.csnn_net(T=4)
+    for layer, lp in zip(spaced["layers"], (6, 5, 5)):
+        layer["log2_p"] = lp
     nets = {  # network, neurons per image (one bootstrap input each), image generator
         "csnn": (synth.csnn_net(T=4), 1152 + 128 + 10, synth.stroke_images),
         "csnn_two_pbs": (two, 1152 + 128 + 10, synth.stroke_images),
         "paper_csnn": (synth.paper_csnn_net(T=2), 1440 + 160 + 10, synth.stroke_images),
         "poisson": (synth.poisson_fc_net(T=20), 784 + 160 + 10, px16),
+        "csnn_spaces": (spaced, 1152 + 128 + 10, synth.stroke_images),
     }
     keys = fhe.keygen_from_seed(P, seed=3, max_batch=18432)
     stream = torch.cuda.current_stream()

@@ -275,3 +275,50 @@ def test_csnn_layer_spaces_full_size_tc_equals_exact(fhe):
     assert np.array_equal(res["EXACT"][0], res["TC"][0])
     assert np.array_equal(res["EXACT"][1], res["TC"][1])
     assert K.status() == fhe.FHE_OK
+
+
+def test_layer_spaces_cut_bootstrap_failures(fhe, oracle_keys):
+    """Measured per-layer bootstrap failures of the conv-SNN at the
+    production ring, one step, 8 images: every layer's decrypted spikes
+    against the plaintext layer applied to the spikes it actually received
+    (so layer l's count holds only its own bootstrap failures).  With the
+    key-switching precision of this set (2^-14) the noise of a WeightSum over
+    hundreds of inputs spans about a message box at p = 64; halving p for
+    layers 1 and 2 (their spaces p = 32) doubles the box and must cut layer
+    1's failures."""
+    import json
+
+    P, K = gpu_keys(fhe, "P630", 3)
+    _, OK = oracle_keys("P630", 3)
+    W = P["n"] + 1
+    B = 8
+    imgs = synth.stroke_images(5, B).reshape(B, -1)
+    ct = fhe.encrypt(K, imgs.reshape(-1), seed=11).view(B, 28 * 28, W)
+    sizes = (1152, 128, 10)
+    rates = {}
+    for lps in ((6, 6, 6), (6, 5, 5)):
+        net = synth.csnn_net(T=1)
+        for layer, lp in zip(net["layers"], lps):
+            layer["log2_p"] = lp
+        snn = make_snn(fhe, K, net, B, "TC")
+        sc = torch.empty((B, 10, W), dtype=torch.int32, device="cuda")
+        snn.infer(ct, B, sc)
+        spk = []
+        for li, size in enumerate(sizes):
+            t = torch.empty((B, size, W), dtype=torch.int32, device="cuda")
+            snn.layer_spikes(li, t)
+            reads = lps[li + 1] if li + 1 < 3 else P["log2_p"]
+            spk.append(O.decrypt(dict(P, log2_p=reads), OK, u32(t).reshape(-1, W)).reshape(B, size))
+        snn.free()
+        miss = [0, 0, 0]
+        for i in range(B):
+            for li, layer in enumerate(net["layers"]):
+                one = dict(net, layers=[layer], static_input=(li == 0))
+                x = imgs[i] if li == 0 else spk[li - 1][i][None]
+                ref = O.snn_plain(P, one, x)["spikes"][0][0]
+                miss[li] += int(np.count_nonzero(ref != spk[li][i]))
+        rates[str(lps)] = [m / (B * s) for m, s in zip(miss, sizes)]
+    print(json.dumps({"bootstrap_failure_rate_per_layer": rates}))
+    uni, spaced = rates["(6, 6, 6)"], rates["(6, 5, 5)"]
+    assert spaced[1] < uni[1]
+    assert K.status() == fhe.FHE_OK
