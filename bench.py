@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # of the bench's own size, from the ncu captures summarised in
 # profiles/blind_rotate_*_p630.md.  Set to None whenever the kernel changes
 # until re-captured.
-TRAFFIC_BYTES = {"tc": (625840393984 + 121506430720 + 621329120000 + 121505306624) / 2,
+TRAFFIC_BYTES = {"tc": (619979249664 + 121526437376 + 623983272192 + 121485164288) / 2,
                  "exact": 34.066688e6 + 16.64e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 
