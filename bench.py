@@ -41,7 +41,7 @@ SM_MAX_MHZ = 2070.0
 # profiles/blind_rotate_*_p630.md.  Set to None whenever the kernel changes
 # until re-captured.
 TRAFFIC_BYTES = {"tc": (619979249664 + 121526437376 + 623983272192 + 121485164288) / 2,
-                 "exact": 34.066688e6 + 16.64e3}
+                 "exact": 34.000896e6 + 6.912e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 
 
