@@ -79,16 +79,19 @@ def test_sample_extract_exact(oracle_keys):
     assert ph == int(O.glwe_phase(P, K, glwe)[0])
 
 
-def test_key_switch_noise_closed_form(oracle_keys):
+@pytest.mark.parametrize("name,samples", [("P64", 1500), ("P630", 1000)])
+def test_key_switch_noise_closed_form(oracle_keys, name, samples):
     """KS: phase_s(out) = phase_z(in) + e with
-    Var e = kN/2 * (2^(32 - lks*log2 Bks))^2/12 + kN*lks*(Bks^2+2)/12 * sigma^2."""
-    P, K = oracle_keys("P64", 7)
+    Var e = kN/2 * (2^(32 - lks*log2 Bks))^2/12 + kN*lks*(Bks^2+2)/12 * sigma^2.
+    At P630 (Bks = 2^2, lks = 7: 14 bits kept) the rounding term dominates,
+    sigma ~ 2^20.7: the per-output noise that a WeightSum then multiplies."""
+    P, K = oracle_keys(name, 7)
     n, kN = P["n"], P["k"] * P["N"]
     g = np.random.default_rng(6)
     z = K["glwe_key"].astype(np.int64)
     s = K["lwe_key"].astype(np.int64)
     errs = []
-    for _ in range(1500):
+    for _ in range(samples):
         big = g.integers(0, 2 ** 32, kN + 1, dtype=np.uint64).astype(np.uint32)
         ph_z = (int(big[-1]) - int(big[:-1].astype(np.int64) @ z)) & MASK32
         out = O.key_switch(P, K, big)
