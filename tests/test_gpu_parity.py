@@ -259,6 +259,28 @@ def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
     assert K.status() == fhe.FHE_OK
 
 
+def test_tc_matches_exact_across_workspace_chunks(fhe, oracle_keys):
+    """A batch larger than the key handle's workspace (16384 ciphertexts)
+    runs in two chunks (a full wave-sized chunk, then a ragged one of 2000):
+    every output of both tables bit-identical between the tensor-core and
+    CUDA-core paths, the outputs on both sides of the chunk edge and at the
+    ends bit-identical to the oracle."""
+    P, K = gpu_keys(fhe, "P630", 3)
+    _, OK = oracle_keys("P630", 3)
+    count = 16384 + 2000
+    m = synth.uniform_messages(43, count, 1 << P["log2_p"])
+    ct = fhe.encrypt(K, m, seed=9)
+    luts = _luts(P, 2)
+    lut = fhe.lut_create(K, luts)
+    ref_gpu = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
+    got = u32(pbs(fhe, K, ct, lut, "TC"))
+    assert np.array_equal(got, ref_gpu)
+    idx = np.array([0, 16383, 16384, count - 1])
+    ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
+    assert np.array_equal(got[:, idx], ref)
+    assert K.status() == fhe.FHE_OK
+
+
 def test_csnn_full_size_layer_chain_tc(fhe, oracle_keys):
     """The bench's network at full size (P630, conv 1->8 5x5 s2 -> FC
     1152->128 -> FC 128->10, 7 images, tensor cores), T = 1 so that every
