@@ -304,8 +304,9 @@ class Lut:
             self.L = tabs[0].shape[0]
             flat = np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in tabs]))
             lp_out = np.ascontiguousarray(np.asarray(log2_p_out, np.uint32).reshape(-1))
-            if len(tabs) != self.groups or lp_out.shape[0] != self.groups * self.L:
-                raise ValueError("one table group and L output spaces per input space")
+            if (len(tabs) != self.groups or lp_out.shape[0] != self.groups * self.L
+                    or any(t.shape[0] != self.L for t in tabs)):
+                raise ValueError("one group of L tables and L output spaces per input space")
             _check(lib().fhe_lut_create_spaces(keys.handle, flat.ctypes.data_as(ctypes.c_void_p),
                                                self.L, self.groups,
                                                lp_in.ctypes.data_as(ctypes.c_void_p),
