@@ -205,10 +205,21 @@ int fhe_pbs_batch_groups(fhe_keys *keys, const uint32_t *ct_in, size_t count, co
  * key handle the smallest batch from which the tensor-core path is faster
  * (written to *tc_min_batch; UINT64_MAX when the tensor-core path is not
  * built for these parameters).  Before tuning, AUTO uses tensor cores from
- * 1024 ciphertexts.  Synchronous; allocates and frees temporary buffers;
+ * 1024 ciphertexts.  It also times the two tile shapes of the tensor-core
+ * path (a 256-ciphertext tile on a cluster of 4 or of 8 SMs) at 1, 4 and the
+ * most tiles that fit at once in clusters of 8, and keeps clusters of 8 only
+ * up to where they were measured no slower (before tuning: whenever the
+ * batch fits).  Synchronous; allocates and frees temporary buffers;
  * takes seconds (longest at N = 2048).  Errors: FHE_EINVAL, FHE_ENOMEM,
  * FHE_ECUDA, FHE_ETIMEOUT. */
 int fhe_pbs_autotune(fhe_keys *keys, uint64_t *tc_min_batch, void *stream);
+
+/* What FHE_VARIANT_AUTO and the tensor-core path currently use: the batch
+ * size from which AUTO picks tensor cores (UINT64_MAX: never) and the most
+ * 256-ciphertext tiles a batch may have to run on clusters of 8 (the device
+ * limit before fhe_pbs_autotune; 0: never; -1: the device limit, not yet
+ * queried).  Host only.  Errors: FHE_EINVAL. */
+int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles);
 
 /* Bootstrapping that allocates nothing (no counterpart in the paper: an
  * integration aid).  Some callers cannot call cudaMalloc at the point where

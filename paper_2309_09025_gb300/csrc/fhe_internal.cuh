@@ -128,6 +128,11 @@ struct fhe_keys {
   // clusters of 8 CTAs of the tensor-core kernel the device holds at once
   // (-1: not queried yet)
   int tc_cl8_max;
+  // batches of up to this many 256-ciphertext tiles run on clusters of 8
+  // (set by fhe_pbs_autotune from timings; -1: up to tc_cl8_max)
+  int tc_cl8_tiles;
+  // autotuner only: force clusters of 4 or 8 (0: the rule above)
+  int tc_force_cl;
   // tensor-core key layout (built on first use of FHE_VARIANT_TC)
   void *d_bsk_tc;
   size_t bsk_tc_bytes;

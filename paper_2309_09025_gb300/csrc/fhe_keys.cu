@@ -188,6 +188,8 @@ extern "C" int fhe_keygen_from_seed(const fhe_params *prm, uint64_t seed, size_t
   // until fhe_pbs_autotune measures it: tensor cores from four cluster tiles up
   K->tc_min_batch = fhe::tc_available(P) ? 1024u : SIZE_MAX;
   K->tc_cl8_max = -1;
+  K->tc_cl8_tiles = -1;
+  K->tc_force_cl = 0;
   const uint64_t bsk_words = (uint64_t)P.n * P.ggsw_words();
   const uint64_t ksk_words = (uint64_t)P.k * P.N * P.l_ks * (P.n + 1u);
   bool ok = cudaMalloc(&K->d_lwe_key, sizeof(uint32_t) * P.n) == cudaSuccess &&

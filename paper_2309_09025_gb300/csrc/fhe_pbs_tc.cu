@@ -826,8 +826,12 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
     const LutArgs la = lut_args(lut, seg_end, s0);
     const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
     // a batch that fits in one wave of 8-CTA clusters runs with half the work
-    // per CTA and step (lower latency); larger ones use the 36 clusters of 4
-    const bool eight = (int)tiles <= K->tc_cl8_max;
+    // per CTA and step (lower latency); larger ones use the 36 clusters of 4.
+    // The autotuner may lower the limit where it measured clusters of 4 faster.
+    const int limit = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
+                                                                               : K->tc_cl8_max;
+    const bool eight = K->tc_force_cl ? (K->tc_force_cl == 8 && (int)tiles <= K->tc_cl8_max)
+                                      : (int)tiles <= limit;
     const bool prof = (s0 == 0) && K->prof_ev0;
     if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
     (eight ? kern8 : kern4)<<<tiles * (eight ? 8u : 4u), kThreads, S.total, st>>>(
@@ -898,6 +902,38 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
       wins = 0;
     }
   }
+  // cluster shape of the tensor-core tiles: a batch of t tiles (t up to the
+  // clusters of 8 the device holds) runs on t clusters of 8 (half the work
+  // per CTA and step) or t clusters of 4; time both at t = 1, 4 and the
+  // largest t, and keep clusters of 8 up to the largest sampled t at and
+  // below which they were never slower
+  int cl8_tiles = -1;
+  if (ok && rc == FHE_OK && K->tc_cl8_max > 0 && cmax >= 256u) {
+    std::vector<int> samples;  // 1, 4 and the largest t, those that fit
+    for (int t : {1, 4, K->tc_cl8_max})
+      if (t <= K->tc_cl8_max && (size_t)t * 256u <= cmax && (samples.empty() || t > samples.back()))
+        samples.push_back(t);
+    cl8_tiles = 0;
+    for (int v = 0; v < 2 && rc == FHE_OK; ++v) {  // warm both instances
+      K->tc_force_cl = v ? 8 : 4;
+      rc = fhe::pbs_run(K, d_in, 256u, lut, d_out, 256u * W, FHE_VARIANT_TC, st);
+    }
+    for (size_t si = 0; si < samples.size() && ok && rc == FHE_OK; ++si) {
+      const size_t c = (size_t)samples[si] * 256u;
+      float t[2] = {0.f, 0.f};
+      for (int v = 0; v < 2 && ok && rc == FHE_OK; ++v) {
+        K->tc_force_cl = v ? 8 : 4;
+        ok = cudaEventRecord(e0, st) == cudaSuccess;
+        rc = fhe::pbs_run(K, d_in, c, lut, d_out, c * W, FHE_VARIANT_TC, st);
+        ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&t[v], e0, e1) == cudaSuccess;
+      }
+      if (!ok || rc) break;
+      if (t[1] > t[0]) break;
+      cl8_tiles = samples[si];
+    }
+    K->tc_force_cl = 0;
+  }
   if (!ok && rc == FHE_OK) { (void)cudaGetLastError(); rc = FHE_ECUDA; }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -905,8 +941,17 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
   cudaFree(d_out);
   fhe_lut_free(lut);
   if (rc) return rc;
+  K->tc_cl8_tiles = cl8_tiles;
   // tensor cores never won up to cmax: use them only above it
   K->tc_min_batch = (best == SIZE_MAX) ? 2 * cmax : best;
   *tc_min_batch = K->tc_min_batch;
   return fhe_status(K, stream);
+}
+
+extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles) {
+  if (!K || !tc_min_batch || !tc_cl8_tiles) return FHE_EINVAL;
+  *tc_min_batch = (K->tc_min_batch == SIZE_MAX) ? UINT64_MAX : (uint64_t)K->tc_min_batch;
+  *tc_cl8_tiles = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
+                                                                           : K->tc_cl8_max;
+  return FHE_OK;
 }

@@ -39,7 +39,7 @@ EXPORTED = (
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
     "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
-    "fhe_lut_create_spaces", "fhe_pbs_batch_groups",
+    "fhe_lut_create_spaces", "fhe_pbs_batch_groups", "fhe_pbs_tuning",
 )
 LUT_MAX_GROUPS = 8
 PBS_NOALLOC_MAX_WORDS = 1 << 20
@@ -133,6 +133,7 @@ def lib():
             "fhe_pbs_autotune": (ctypes.c_int, [vp, ctypes.POINTER(u64), vp]),
             "fhe_lut_create_spaces": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(vp)]),
             "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
+            "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -227,6 +228,13 @@ class Keys:
         v = ctypes.c_uint64()
         _check(lib().fhe_pbs_autotune(self.handle, ctypes.byref(v), _stream(stream)), "pbs_autotune")
         return None if v.value == (1 << 64) - 1 else int(v.value)
+
+    def tuning(self):
+        """fhe_pbs_tuning: (smallest batch AUTO runs on tensor cores or None,
+        most tiles run on clusters of 8)."""
+        v, c = ctypes.c_uint64(), ctypes.c_int32()
+        _check(lib().fhe_pbs_tuning(self.handle, ctypes.byref(v), ctypes.byref(c)), "pbs_tuning")
+        return (None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value)
 
 
 def keygen_from_seed(params, seed, max_batch=0, stream=None):

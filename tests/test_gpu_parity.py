@@ -389,15 +389,22 @@ def test_snn_toy_layer_fft_decrypts_like_plain(fhe, oracle_keys):
 def test_autotuned_variant_is_bit_exact(fhe, oracle_keys, name):
     """FHE_VARIANT_AUTO picks the CUDA-core or tensor-core blind rotation by
     batch size (crossover measured by fhe_pbs_autotune); on both sides of the
-    crossover the outputs equal the CUDA-core path's bit for bit.  P64 has no
+    crossover the outputs equal the CUDA-core path's bit for bit.  The tuner
+    also times the two tile shapes of the tensor-core path (clusters of 4 or
+    8 SMs per 256-ciphertext tile) and reports the limit it keeps.  P64 has no
     tensor-core path: the tuner reports none and AUTO stays on CUDA cores."""
     P, K = gpu_keys(fhe, name, 3)
     p = 1 << P["log2_p"]
     cross = K.autotune()
+    tuned, cl8_tiles = K.tuning()
+    assert tuned == cross
     if name == "P64":
         assert cross is None
     else:
         assert cross is not None and 128 <= cross <= 8192
+        assert 0 <= cl8_tiles <= 152 // 8
+        print("autotune %s: tensor cores from %d ciphertexts, clusters of 8 up to %d tiles"
+              % (name, cross, cl8_tiles))
     luts = _luts(P, 2)
     lut = fhe.lut_create(K, luts)
     for count in (100, 1500):
