@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # of the bench's own size, from the ncu captures summarised in
 # profiles/blind_rotate_*_p630.md.  Set to None whenever the kernel changes
 # until re-captured.
-TRAFFIC_BYTES = {"tc": (619979249664 + 121526437376 + 623983272192 + 121485164288) / 2,
+TRAFFIC_BYTES = {"tc": (615122137600 + 118857882880 + 615460810496 + 118847958272) / 2,
                  "exact": 34.000896e6 + 6.912e3}
 # Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
 

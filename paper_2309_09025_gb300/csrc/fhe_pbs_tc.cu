@@ -186,17 +186,31 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive 32-bit TMEM columns of the warp's 32 lanes, completed by the
+// next tc_wait16 on the same registers.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Waits for this thread's outstanding TMEM loads; the registers are operands
+// so that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tc_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+// outv[k] += int(r[k]) << shift for the 16 drained fp32 sums (exact integers).
+__device__ __forceinline__ void tc_acc16(uint32_t *outv, const uint32_t (&r)[16], uint32_t shift) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) outv[k] += (uint32_t)__float2int_rn(__uint_as_float(r[k])) << shift;
 }
 
 // Shared-memory matrix descriptor: SWIZZLE_NONE, K-major, version 1.
@@ -660,15 +674,19 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
               for (uint32_t z = 0; z < 2u; ++z) {
                 const uint32_t shift = 8u * (2u * lp + z) + sub;
                 const uint32_t tbase = tmem + ((32u * quarter) << 16) + z * (uint32_t)kBN + half * 128u;
+                // two 16-column buffers: the load of one overlaps the
+                // conversion of the other
+                uint32_t ra[16], rb[16];
+                tc_ld16(tbase, ra);
+                tc_wait16(ra);
 #pragma unroll
-                for (uint32_t part = 0; part < 4u; ++part) {
-                  uint32_t r[32];
-                  tc_ld32(tbase + part * 32u, r);
-#pragma unroll
-                  for (int k = 0; k < 32; ++k) {
-                    const int32_t v = __float2int_rn(__uint_as_float(r[k]));
-                    outv[part * 32 + k] += (uint32_t)v << shift;
-                  }
+                for (uint32_t c = 0; c < 8u; c += 2u) {
+                  tc_ld16(tbase + (c + 1u) * 16u, rb);
+                  tc_acc16(outv + c * 16u, ra, shift);
+                  tc_wait16(rb);
+                  if (c + 2u < 8u) tc_ld16(tbase + (c + 2u) * 16u, ra);
+                  tc_acc16(outv + (c + 1u) * 16u, rb, shift);
+                  if (c + 2u < 8u) tc_wait16(ra);
                 }
               }
             }
