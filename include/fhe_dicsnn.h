@@ -214,6 +214,28 @@ int fhe_pbs_batch_groups(fhe_keys *keys, const uint32_t *ct_in, size_t count, co
  * FHE_ECUDA, FHE_ETIMEOUT. */
 int fhe_pbs_autotune(fhe_keys *keys, uint64_t *tc_min_batch, void *stream);
 
+/* Exactness plan of the tensor-core blind rotation for a parameter set (no
+ * counterpart in the paper; host only, no device needed).  The external
+ * product runs on fp16 tensor cores with fp32 accumulation: key words are
+ * four balanced 8-bit limbs (|limb| <= 128), gadget digits are balanced
+ * (|d| <= Bg/2) or, when Bg/2 * 128 * N exceeds 2^24, split into two
+ * sub-digits of sub_shift bits; the fp32 accumulator is drained after every
+ * chunk_rows digit rows, so that no partial sum exceeds max_partial <= 2^24
+ * and every fp32 result is the exact integer.  available = 0 when the path
+ * does not cover the set (N not 1024 or 2048, digits that do not fit).
+ * Errors: FHE_EINVAL (null pointer, parameters the library does not support
+ * at all, as fhe_keygen_from_seed). */
+typedef struct fhe_tc_plan {
+  int32_t available;     /* 1: FHE_VARIANT_TC covers these parameters        */
+  uint32_t key_rows;     /* (k+1) l GGSW rows                                */
+  uint32_t digit_rows;   /* key_rows, doubled when digits are split          */
+  uint32_t sub_shift;    /* 0, or the bits of the low sub-digit              */
+  uint32_t max_digit;    /* largest |digit| (or |sub-digit|) multiplied      */
+  uint32_t chunk_rows;   /* digit rows accumulated in fp32 per drain         */
+  uint64_t max_partial;  /* max_digit * 128 * chunk_rows * N                 */
+} fhe_tc_plan;
+int fhe_tc_plan_query(const fhe_params *params, fhe_tc_plan *out);
+
 /* What FHE_VARIANT_AUTO and the tensor-core path currently use: the batch
  * size from which AUTO picks tensor cores (UINT64_MAX: never) and the most
  * 256-ciphertext tiles a batch may have to run on clusters of 8 (the device

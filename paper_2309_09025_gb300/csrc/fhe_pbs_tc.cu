@@ -973,3 +973,18 @@ extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t
                                                                            : K->tc_cl8_max;
   return FHE_OK;
 }
+
+extern "C" int fhe_tc_plan_query(const fhe_params *params, fhe_tc_plan *out) {
+  if (!params || !out) return FHE_EINVAL;
+  const Params P = fhe::from_abi(*params);
+  if (!fhe::params_supported(P)) return FHE_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->available = tc_supported(P) ? 1 : 0;
+  out->key_rows = P.rows();
+  out->digit_rows = tc_digit_rows(P);
+  out->sub_shift = tc_sub_shift(P);
+  out->max_digit = out->sub_shift ? (1u << (out->sub_shift - 1u)) : (1u << (P.log2_bg - 1u));
+  out->chunk_rows = tc_chunk_r(P);
+  out->max_partial = (uint64_t)out->max_digit * 128u * out->chunk_rows * P.N;
+  return FHE_OK;
+}

@@ -39,7 +39,7 @@ EXPORTED = (
     "fhe_pbs_batch_noalloc", "fhe_snn_begin", "fhe_snn_step", "fhe_snn_end",
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
     "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
-    "fhe_lut_create_spaces", "fhe_pbs_batch_groups", "fhe_pbs_tuning",
+    "fhe_lut_create_spaces", "fhe_pbs_batch_groups", "fhe_pbs_tuning", "fhe_tc_plan_query",
 )
 LUT_MAX_GROUPS = 8
 PBS_NOALLOC_MAX_WORDS = 1 << 20
@@ -73,6 +73,13 @@ class LayerDesc(ctypes.Structure):
                 ("cout", ctypes.c_uint32), ("kh", ctypes.c_uint32), ("kw", ctypes.c_uint32),
                 ("stride", ctypes.c_uint32), ("pad", ctypes.c_uint32),
                 ("log2_p", ctypes.c_uint32)]
+
+
+class TcPlan(ctypes.Structure):
+    _fields_ = [("available", ctypes.c_int32), ("key_rows", ctypes.c_uint32),
+                ("digit_rows", ctypes.c_uint32), ("sub_shift", ctypes.c_uint32),
+                ("max_digit", ctypes.c_uint32), ("chunk_rows", ctypes.c_uint32),
+                ("max_partial", ctypes.c_uint64)]
 
 
 class SnnDesc(ctypes.Structure):
@@ -134,6 +141,7 @@ def lib():
             "fhe_lut_create_spaces": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(vp)]),
             "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
             "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32)]),
+            "fhe_tc_plan_query": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(TcPlan)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -235,6 +243,15 @@ class Keys:
         v, c = ctypes.c_uint64(), ctypes.c_int32()
         _check(lib().fhe_pbs_tuning(self.handle, ctypes.byref(v), ctypes.byref(c)), "pbs_tuning")
         return (None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value)
+
+
+def tc_plan(params):
+    """fhe_tc_plan_query: the tensor-core path's exactness plan for a
+    parameter dict (host only)."""
+    p = Params.from_dict(params)
+    out = TcPlan()
+    _check(lib().fhe_tc_plan_query(ctypes.byref(p), ctypes.byref(out)), "tc_plan_query")
+    return {f: int(getattr(out, f)) for f, _ in TcPlan._fields_}
 
 
 def keygen_from_seed(params, seed, max_batch=0, stream=None):
