@@ -218,7 +218,7 @@ def test_test_poly_box_lookup():
 
 
 def test_multi_value_output_noise(oracle_keys):
-    """Multi-value PBS output error (4.3: one rotation of TV0, then r_j * ACC,
+    """Multi-value PBS output error (4.2, read as one blind rotation of TV0, then r_j * ACC,
     extraction, key switch).  r_j * X^(-phi~) TV0 = X^(-phi~) Delta coeffs_j, so
     the noiseless phase is coefficient 0 of X^(-phi~) TV_j; the error is
     (r_j * E_BR)[0] + e_KS with variance ||r_j||^2 Var_BR + Var_KS.  The sample
