@@ -39,3 +39,39 @@ def test_unsupported_params_rejected_before_any_device_work():
     assert rc == fhe.FHE_EINVAL and not h.value
     rc = fhe.lib().fhe_keygen_from_seed(None, 1, 0, None, ctypes.byref(h))
     assert rc == fhe.FHE_EINVAL
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of the ABI structs have the header's
+    size and field offsets (a C probe compiled with the host compiler
+    against include/fhe_dicsnn.h prints them)."""
+    import shutil
+    import subprocess
+
+    import pytest
+
+    from paper_2309_09025_gb300 import fhe
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"fhe_params": fhe.Params, "fhe_layer_desc": fhe.LayerDesc,
+               "fhe_snn_desc": fhe.SnnDesc, "fhe_tc_plan": fhe.TcPlan}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fhe_dicsnn.h"',
+             "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (cname, field, cname, field))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
