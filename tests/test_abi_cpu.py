@@ -75,3 +75,32 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of the header has the same value in the binding
+    (FHE_X there is FHE_X, X or a listed alias here)."""
+    from paper_2309_09025_gb300 import fhe
+    text = open(os.path.join(ROOT, "include", "fhe_dicsnn.h")).read()
+    defines = dict(re.findall(r"#define (FHE_[A-Z0-9_]+) ([^/\n]+)", text))
+    defines.pop("FHE_DICSNN_H", None)
+    alias = {"FHE_KEY_LWE": "KEY_LWE", "FHE_KEY_GLWE": "KEY_GLWE", "FHE_KEY_BSK": "KEY_BSK",
+             "FHE_KEY_KSK": "KEY_KSK", "FHE_LAYER_FC": "LAYER_FC", "FHE_LAYER_CONV": "LAYER_CONV",
+             "FHE_LAYER_POISSON": "LAYER_POISSON", "FHE_LIF_MULTI_VALUE": "LIF_MULTI_VALUE",
+             "FHE_LIF_TWO_PBS": "LIF_TWO_PBS", "FHE_SNN_PROFILE": "SNN_PROFILE",
+             "FHE_LUT_MAX_GROUPS": "LUT_MAX_GROUPS",
+             "FHE_PBS_NOALLOC_MAX_WORDS": "PBS_NOALLOC_MAX_WORDS"}
+    assert len(defines) >= 20
+    def value_of(expr):  # "0", "(-1)", "(1u << 20)"
+        e = expr.strip().strip("()").replace("u", "")
+        if "<<" in e:
+            a, b = e.split("<<")
+            return int(a) << int(b)
+        return int(e)
+
+    for name, expr in defines.items():
+        value = value_of(expr)
+        py = getattr(fhe, name, None)
+        if py is None:
+            py = getattr(fhe, alias.get(name, name[len("FHE_"):]))
+        assert py == value, name
