@@ -400,7 +400,13 @@ def pbs_batch_noalloc(keys, ct_in, lut, out=None, stream=None):
 
 
 class Snn:
-    """Encrypted DiCSNN (fhe_snn_create / fhe_snn_infer)."""
+    """Encrypted DiCSNN (fhe_snn_create / fhe_snn_infer).
+
+    net: {"layers": [...], "lif": {"v_th", "leak_shift", "spike_scale"}, "T",
+    "static_input", optional "lif_mode" ("multi" or "two_pbs")}; a layer is
+    {"type": "fc", "W": [out][in]}, {"type": "conv", "W": [cout][cin][kh][kw],
+    "h", "w", "stride", "pad"} or {"type": "poisson", "M": [T][pixels]}, with
+    an optional "log2_p" giving the layer its own message space."""
 
     def __init__(self, keys, net, max_images, variant=VARIANT_EXACT, use_graph=True,
                  profile=False):
