@@ -104,3 +104,45 @@ def test_binding_constants_match_the_header():
         if py is None:
             py = getattr(fhe, alias.get(name, name[len("FHE_"):]))
         assert py == value, name
+
+
+def test_plain_c_client_builds_links_and_fails_cleanly_without_gpu(tmp_path):
+    """tests/c_abi_example.c, a plain C client of the ABI (keys, encryption,
+    one multi-value bootstrap batch, decryption, check against the tables),
+    compiles against the header and links against the library.  Without a
+    GPU it must stop at the first call with the library's error code (exit 2,
+    the failing call named), not crash; with one it must find every output
+    equal to its table value (exit 0)."""
+    import shutil
+    import subprocess
+
+    import pytest
+
+    from paper_2309_09025_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if cc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.exists(d)), None)
+    exe = tmp_path / "c_abi_example"
+    cmd = [cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(ROOT, "tests", "c_abi_example.c"),
+           "-o", str(exe), "-L", libdir, "-lfhe_dicsnn", "-Wl,-rpath," + libdir]
+    if cudalib:
+        cmd += ["-L", cudalib, "-Wl,-rpath," + cudalib]
+    cmd += ["-lcudart"]
+    subprocess.run(cmd, check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    try:
+        import torch
+        gpu = torch.cuda.is_available()
+    except ImportError:
+        gpu = False
+    if gpu:
+        assert r.returncode == 0, r.stdout + r.stderr
+    else:
+        assert r.returncode == 2, r.stdout + r.stderr
+        assert "fhe_keygen_from_seed" in r.stderr
