@@ -44,9 +44,12 @@ extern "C" int fhe_pbs_batch_noalloc(const fhe_keys *K, const uint32_t *ct_in, s
                                      const fhe_lut *lut, uint32_t *ct_out, void *stream) {
   if (!K || !lut || (count && (!ct_in || !ct_out)) || lut->N != K->P.N || lut->groups != 1u)
     return FHE_EINVAL;
+  if (lut->L == 0u) return FHE_EINVAL;
   if (!count) return FHE_OK;
-  const uint64_t words = (uint64_t)lut->L * count * K->P.big_words();
-  if (words > (uint64_t)FHE_PBS_NOALLOC_MAX_WORDS) return FHE_EINVAL;
+  // L * count * (kN + 1) <= the array's size, checked by division so that no
+  // product can wrap for a huge count
+  const uint64_t per_ct = (uint64_t)lut->L * K->P.big_words();
+  if ((uint64_t)count > (uint64_t)FHE_PBS_NOALLOC_MAX_WORDS / per_ct) return FHE_EINVAL;
   int dev = 0;
   FHE_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != K->device) return FHE_EINVAL;
