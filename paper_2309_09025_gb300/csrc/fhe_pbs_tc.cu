@@ -141,28 +141,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, uint32_t bytes,
-                                                   uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Completion of every tcgen05.mma this thread issued arrives on the barrier at
-// the same offset in each CTA of `mask`.
-__device__ __forceinline__ void tc2_commit_multicast(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 // D[256 x N] (+)= A[256 x 16] B[16 x N] over the CTA pair: rows 0..127 of A
 // and D live in the leader CTA, rows 128..255 in its peer; each CTA holds
@@ -181,6 +164,39 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
   return r;
 }
+// Completion of every tcgen05.mma this thread issued arrives on the barrier at
+// the same offset in each CTA of `mask`: one commit per CTA (the single-GPU
+// build uses one multicast commit instead, fhe_tc_multicast.cuh).
+__device__ __forceinline__ void tc2_commit_each(uint64_t *bar, uint16_t mask) {
+  for (uint32_t r = 0; r < 16u; ++r)
+    if (mask & (1u << r))
+      asm volatile(
+          "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              cluster_addr(bar, r))
+          : "memory");
+}
+// One digit tile (kATile bytes, 128 rows x 128 K) into an A stage.  Per-CTA
+// form: this CTA copies the whole tile into its own shared memory.  The
+// cluster-multicast form (MC = true, defined in fhe_tc_multicast.cuh and
+// compiled only into single-GPU builds) copies the share this CTA generated
+// into the same stage of every CTA that holds the same rows.
+template <bool MC>
+struct ATileLoad {
+  static __device__ __forceinline__ void run(unsigned char *stage, const __half *tile, uint32_t pr,
+                                             uint32_t np, uint64_t *bar, uint16_t mask) {
+    (void)pr; (void)np; (void)mask;
+    bulk_g2s(stage, tile, (uint32_t)kATile, bar);
+  }
+};
+#ifndef FHE_NO_MULTICAST
+#include "fhe_tc_multicast.cuh"
+constexpr bool kTcMulticast = true;
+#else
+constexpr bool kTcMulticast = false;
+__device__ __forceinline__ void tc2_commit_ctas(uint64_t *bar, uint16_t mask) {
+  tc2_commit_each(bar, mask);
+}
+#endif
 // Arrive on a barrier of another CTA of the cluster (default semantics; the
 // operands it announces were written by the async proxy and are read by the
 // tensor core, which the barrier phase alone orders).
@@ -293,7 +309,7 @@ __host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) 
 // CL = CTAs per cluster: 4 (two pairs, one per output polynomial) or 8 (four
 // pairs, each with half the blocks of one polynomial: half the work per CTA
 // and step, for batches that fit in the 15 clusters of 8 the GPU holds).
-template <int N, int CL>
+template <int N, int CL, bool MC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
                       const uint32_t *__restrict__ ct_in, size_t count,
@@ -548,6 +564,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     if (warp == 0 || warp == kBWarp) {
       // producers: warp 0 streams the digit tiles, warp kBWarp the key windows
       if (lane == 0) {
+        // per-CTA tile copies also read the rows other CTAs generated (their
+        // generic stores were fenced for the async proxy before the barrier)
+        if (!MC) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
           const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
           for (uint32_t lp = 0; lp < 2u; ++lp)
@@ -575,10 +594,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                     if (a_it >= kAStages)
                       wait_bounded(&a_empty[as], ((a_it / kAStages) - 1u) & 1u, &s_abort);
                     if (!s_abort) {
-                      const __half *src = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H + pr * (TILE_H / NP);
+                      const __half *tsrc = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H;
                       mbar_expect_tx(&a_full[as], kATile);
-                      bulk_g2s_multicast(sA + as * kATile + pr * (kATile / NP), src, kATile / NP,
-                                         &a_full[as], a_mask);
+                      ATileLoad<MC>::run(sA + as * kATile, tsrc, pr, NP, &a_full[as], a_mask);
                     }
                     ++a_it;
                   }
@@ -618,14 +636,14 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                         }
                         accum = 1u;
                       }
-                      tc2_commit_multicast(&a_empty[as], all_mask);
+                      tc2_commit_ctas(&a_empty[as], all_mask);
                     }
                     ++a_it;
                   }
-                  if (!s_abort) tc2_commit_multicast(&b_empty[bs], pair_mask);
+                  if (!s_abort) tc2_commit_ctas(&b_empty[bs], pair_mask);
                   ++b_it;
                 }
-              if (!s_abort) tc2_commit_multicast(t_full, pair_mask);
+              if (!s_abort) tc2_commit_ctas(t_full, pair_mask);
               ++u_it;
             }
       } else if (lane == 0) {
@@ -711,7 +729,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   // Every MMA of the pair has completed before TMEM is released (on the
   // normal path the epilogue already waited for all of them).
   if (warp == 1 && lane == 0 && leader) {
-    tc2_commit_multicast(done, (uint16_t)(1u << q));
+    tc2_commit_ctas(done, (uint16_t)(1u << q));
     wait_time_bounded(done, 0u);
   }
 
@@ -827,8 +845,8 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   if (rc) return rc;
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem();
-  auto kern4 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 4> : k_blind_rotate_tc<2048, 4>;
-  auto kern8 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 8> : k_blind_rotate_tc<2048, 8>;
+  auto kern4 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 4, kTcMulticast> : k_blind_rotate_tc<2048, 4, kTcMulticast>;
+  auto kern8 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 8, kTcMulticast> : k_blind_rotate_tc<2048, 8, kTcMulticast>;
   FHE_CUDA_TRY(cudaFuncSetAttribute(kern4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   FHE_CUDA_TRY(cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   if (K->tc_cl8_max < 0) {  // clusters of 8 the device holds at once (once per key handle)

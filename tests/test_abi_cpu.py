@@ -146,3 +146,25 @@ def test_plain_c_client_builds_links_and_fails_cleanly_without_gpu(tmp_path):
     else:
         assert r.returncode == 2, r.stdout + r.stderr
         assert "fhe_keygen_from_seed" in r.stderr
+
+
+def test_replica_build_compiles_no_multicast():
+    """Runs with one process per GPU load the replica library; every source
+    it compiles, preprocessed with its flags, holds no multicast copy or
+    multicast commit (the single-GPU forms live in fhe_tc_multicast.cuh,
+    which the replica flags leave out)."""
+    import subprocess
+    from paper_2309_09025_gb300 import build
+    try:
+        nv = build.nvcc()
+    except RuntimeError:
+        pytest.skip("no nvcc")
+    flags = [f for f in build._flags(False, replica=True) if not f.startswith("-gencode")
+             and not f.startswith("arch=")]
+    for src in build.SOURCES:
+        r = subprocess.run([nv, "-E", "-x", "cu"] + build.ARCH + flags +
+                           [os.path.join(build.CSRC, src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        bad = [l for l in r.stdout.splitlines()
+               if "multicast" in l and ("cp.async" in l or "tcgen05" in l or "asm" in l)]
+        assert not bad, (src, bad[:3])
