@@ -258,7 +258,11 @@ int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8
  * Limit: L * count * (k*N + 1) <= FHE_PBS_NOALLOC_MAX_WORDS, e.g. count <= 511
  * for two tables at N = 1024; larger batches return FHE_EINVAL (split them).
  * The first call on a device resolves the scratch address on that device
- * (make that first call before any stream capture).  All calls share the one
+ * (make that first call before any stream capture).  With CUDA's lazy module
+ * loading (the default), that first call is also where the library's device
+ * code, and with it the 4 MiB array, is loaded onto the device: "allocates
+ * nothing" holds from the first call on; a caller that must not see even
+ * that can make one call with count = 1 at start-up.  All calls share the one
  * array: calls whose work overlaps on the GPU (other streams, other threads)
  * race on it and must be serialized by the caller.
  * Errors: FHE_EINVAL (bad argument, batch above the limit, keys of another
@@ -419,6 +423,32 @@ uint32_t fhe_snn_iterations(const fhe_snn *net);
 int fhe_snn_stream_push(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
                         int on_host, void *stream);
 int fhe_snn_stream_flush(fhe_snn *net, void *stream);
+
+/* The streamed inference one iteration at a time (no counterpart in the
+ * paper: lets a test or a scheduler observe every layer-skewed step of the
+ * same code path as fhe_snn_stream_push).  fhe_snn_stream_stage stages the
+ * next batch (arguments and rules of fhe_snn_stream_push) without running
+ * any step; a batch must be staged before its first step runs (FHE_EINVAL
+ * otherwise).  fhe_snn_stream_push = stage + the steps up to the end of the
+ * staged batch's T steps.  fhe_snn_stream_iterate runs the next step of the
+ * stream (including the last layers' steps after the last staged batch, as
+ * the flush does) and returns how many steps can still run without staging
+ * (0: nothing ran), or a negative error.
+ * fhe_snn_stream_state copies, for batch `batch` (0 = the stream's first
+ * batch) while it holds its slot (staged, and fewer than `slots` batches
+ * staged after it), layer `layer`'s latest spikes (FHE_STATE_SPIKES),
+ * membranes V (FHE_STATE_MEMBRANES) or WeightSum currents I
+ * (FHE_STATE_CURRENTS; a static first layer keeps its step-0 current) to the
+ * device buffer dst [n_images][out_size][n+1] on `stream`.  A Poisson layer
+ * has spikes only.  Errors: FHE_EINVAL, FHE_ECUDA, FHE_ETIMEOUT. */
+#define FHE_STATE_SPIKES 0
+#define FHE_STATE_MEMBRANES 1
+#define FHE_STATE_CURRENTS 2
+int fhe_snn_stream_stage(fhe_snn *net, const uint32_t *ct_input, size_t n_images, uint32_t *scores,
+                         int on_host, void *stream);
+int fhe_snn_stream_iterate(fhe_snn *net, void *stream);
+int fhe_snn_stream_state(const fhe_snn *net, uint64_t batch, uint32_t layer, int kind,
+                         uint32_t *dst, void *stream);
 
 /* Optional: device spike ciphertexts of layer `layer` at the last step of
  * the last inference, copied to device buffer dst [n_images][size][n+1]. */

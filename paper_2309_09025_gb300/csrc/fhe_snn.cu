@@ -746,24 +746,25 @@ static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
   return FHE_OK;
 }
 
-extern "C" int fhe_snn_stream_push(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
-                                   int on_host, void *stream) {
+extern "C" int fhe_snn_stream_stage(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
+                                    int on_host, void *stream) {
   if (!S || !ct_input || !scores || ni == 0 || ni > S->desc.max_images || S->cur_images)
     return FHE_EINVAL;
   int rc = stream_alloc(S);
   if (rc) return rc;
   StreamState &Z = *S->stream;
+  const uint32_t T = S->desc.T, W = S->K->P.n + 1u;
   if (Z.ni == 0) {  // a new stream
     Z.ni = ni;
     Z.pushed = 0;
     Z.next_iter = 0;
     Z.ev_used = 0;
     S->prof_stream = true;
-  } else if (ni != Z.ni) {
+  } else if (ni != Z.ni || Z.next_iter > Z.pushed * T) {
+    // other batch size, or the new batch's first iteration has already run
     return FHE_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const uint32_t T = S->desc.T, W = S->K->P.n + 1u;
   const uint64_t b = Z.pushed;
   const uint32_t sl = (uint32_t)(b % Z.nslots);
   const size_t in_words = ni * (S->desc.static_input ? 1u : T) * S->n_in * W;
@@ -772,11 +773,49 @@ extern "C" int fhe_snn_stream_push(fhe_snn *S, const uint32_t *ct_input, size_t 
   Z.dst[sl] = scores;
   Z.dst_host[sl] = on_host;
   Z.pushed = b + 1u;
-  for (uint64_t j = b * T; j < (b + 1u) * T; ++j) {
-    rc = stream_iteration(S, j, st);
+  return FHE_OK;
+}
+
+extern "C" int fhe_snn_stream_push(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,
+                                   int on_host, void *stream) {
+  int rc = fhe_snn_stream_stage(S, ct_input, ni, scores, on_host, stream);
+  if (rc) return rc;
+  StreamState &Z = *S->stream;
+  const uint64_t end = Z.pushed * S->desc.T;  // the staged batch's T iterations
+  for (uint64_t j = Z.next_iter; j < end; ++j) {
+    rc = stream_iteration(S, j, (cudaStream_t)stream);
     if (rc) return rc;
   }
-  Z.next_iter = (b + 1u) * T;
+  Z.next_iter = end;
+  return FHE_OK;
+}
+
+extern "C" int fhe_snn_stream_iterate(fhe_snn *S, void *stream) {
+  if (!S || !S->stream || !S->stream->ni) return FHE_EINVAL;
+  StreamState &Z = *S->stream;
+  const uint64_t end = Z.pushed * S->desc.T + S->layers.size() - 1u;
+  if (Z.next_iter >= end) return 0;
+  const int rc = stream_iteration(S, Z.next_iter, (cudaStream_t)stream);
+  if (rc) return rc;
+  ++Z.next_iter;
+  return (int)(end - Z.next_iter);
+}
+
+extern "C" int fhe_snn_stream_state(const fhe_snn *S, uint64_t batch, uint32_t layer, int kind,
+                                    uint32_t *dst, void *stream) {
+  if (!S || !dst || !S->stream || !S->stream->ni || layer >= S->layers.size()) return FHE_EINVAL;
+  const StreamState &Z = *S->stream;
+  if (batch >= Z.pushed || Z.pushed > batch + Z.nslots) return FHE_EINVAL;  // not in its slot
+  const uint32_t sl = (uint32_t)(batch % Z.nslots);
+  const bool poisson = S->layers[layer].type == FHE_LAYER_POISSON;
+  const uint32_t *src = nullptr;
+  if (kind == FHE_STATE_SPIKES) src = Z.spk[sl][layer];
+  else if (kind == FHE_STATE_MEMBRANES && !poisson) src = Z.mem[sl][layer];
+  else if (kind == FHE_STATE_CURRENTS && !poisson) src = Z.I[sl][layer];
+  if (!src) return FHE_EINVAL;
+  const size_t words = Z.ni * S->layers[layer].out_size * (S->K->P.n + 1u);
+  FHE_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
   return FHE_OK;
 }
 

@@ -28,6 +28,7 @@ KEY_LWE, KEY_GLWE, KEY_BSK, KEY_KSK = 0, 1, 2, 3
 LAYER_FC, LAYER_CONV, LAYER_POISSON = 0, 1, 2
 LIF_MULTI_VALUE, LIF_TWO_PBS = 0, 1
 SNN_PROFILE = 2
+STATE_SPIKES, STATE_MEMBRANES, STATE_CURRENTS = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = (
@@ -40,6 +41,7 @@ EXPORTED = (
     "fhe_snn_iterations", "fhe_selftest_timeout", "fhe_fft_max_error",
     "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
     "fhe_lut_create_spaces", "fhe_pbs_batch_groups", "fhe_pbs_tuning", "fhe_tc_plan_query",
+    "fhe_snn_stream_stage", "fhe_snn_stream_iterate", "fhe_snn_stream_state",
 )
 LUT_MAX_GROUPS = 8
 PBS_NOALLOC_MAX_WORDS = 1 << 20
@@ -92,16 +94,29 @@ class SnnDesc(ctypes.Structure):
 
 
 _lib = None
+_lib_path = None
+
+
+def use_library(path):
+    """Select the library file before its first use: the replica build
+    (libfhe_dicsnn_replica.so, no cluster-multicast copies) for runs with one
+    process per GPU.  The environment variable FHE_DICSNN_LIB does the same."""
+    global _lib_path
+    if _lib is not None and os.path.abspath(path) != os.path.abspath(_lib_path):
+        raise RuntimeError("the CUDA library is already loaded from " + _lib_path)
+    _lib_path = path
 
 
 def lib():
     """Load the CUDA library (no fallback: raises if it was not built)."""
-    global _lib
+    global _lib, _lib_path
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libfhe_dicsnn.so is missing: run "
-                               "`python -c 'import __graft_entry__ as g; g.build()'`")
-        L = ctypes.CDLL(LIB_PATH)
+        if _lib_path is None:
+            _lib_path = os.environ.get("FHE_DICSNN_LIB") or LIB_PATH
+        if not os.path.exists(_lib_path):
+            raise RuntimeError("%s is missing: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % _lib_path)
+        L = ctypes.CDLL(_lib_path)
         vp, sz, u32, u64, i32 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
                                  ctypes.c_uint64, ctypes.c_int32)
         sig = {
@@ -142,6 +157,9 @@ def lib():
             "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
             "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32)]),
             "fhe_tc_plan_query": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(TcPlan)]),
+            "fhe_snn_stream_stage": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
+            "fhe_snn_stream_iterate": (ctypes.c_int, [vp, vp]),
+            "fhe_snn_stream_state": (ctypes.c_int, [vp, u64, u32, ctypes.c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -495,6 +513,33 @@ class Snn:
         _check(lib().fhe_snn_stream_push(self.handle, pin, n_images, pout, int(bool(on_host)),
                                          _stream(stream)), "snn_stream_push")
         return scores
+
+    def stream_stage(self, ct_input, n_images, scores, on_host=False, stream=None):
+        """Stage the next batch without running a step (fhe_snn_stream_stage)."""
+        if on_host:
+            pin = ctypes.c_void_p(ct_input.data_ptr()) if hasattr(ct_input, "data_ptr") \
+                else ct_input.ctypes.data_as(ctypes.c_void_p)
+            pout = ctypes.c_void_p(scores.data_ptr()) if hasattr(scores, "data_ptr") \
+                else scores.ctypes.data_as(ctypes.c_void_p)
+        else:
+            pin, pout = _ptr(ct_input), _ptr(scores)
+        _check(lib().fhe_snn_stream_stage(self.handle, pin, n_images, pout, int(bool(on_host)),
+                                          _stream(stream)), "snn_stream_stage")
+        return scores
+
+    def stream_iterate(self, stream=None):
+        """Run the stream's next step; returns the steps that can still run."""
+        rc = lib().fhe_snn_stream_iterate(self.handle, _stream(stream))
+        if rc < 0:
+            _check(rc, "snn_stream_iterate")
+        return rc
+
+    def stream_state(self, batch, layer, kind, dst, stream=None):
+        """Copy a streamed batch's layer state (STATE_SPIKES, STATE_MEMBRANES
+        or STATE_CURRENTS) into the device tensor dst."""
+        _check(lib().fhe_snn_stream_state(self.handle, int(batch), int(layer), int(kind), _ptr(dst),
+                                          _stream(stream)), "snn_stream_state")
+        return dst
 
     def stream_flush(self, stream=None):
         """Complete every pushed batch and end the stream."""
