@@ -36,13 +36,36 @@ SM_COUNT = 152
 # INT32 multiply-add issue rate of one SM (4 SMSPs x 16 lanes per clock).
 IMAD_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one blind-rotation launch
-# of the bench's own size, from the ncu captures summarised in
-# profiles/blind_rotate_*_p630.md.  Set to None whenever the kernel changes
-# until re-captured.
-TRAFFIC_BYTES = {"tc": (615122137600 + 118857882880 + 615460810496 + 118847958272) / 2,
-                 "exact": 34.000896e6 + 6.912e3}
-# Blind-rotation MACs per bootstrap: n (k+1)^2 l N^2 (uint32 multiply-adds).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# blind-rotation launch, recorded with the ncu command that measured it and
+# a hash of the kernel's source file: a record whose hash no longer matches
+# the source (the kernel changed since) reports no traffic.
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+KERNEL_SOURCE = {"tc": "paper_2309_09025_gb300/csrc/fhe_pbs_tc.cu",
+                 "exact": "paper_2309_09025_gb300/csrc/fhe_pbs_exact.cu"}
+
+
+def source_sha16(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(arm, cts_per_launch):
+    """Bytes per launch from the traffic record, or (None, why)."""
+    if not os.path.exists(TRAFFIC_RECORD):
+        return None, "no traffic record"
+    sha = source_sha16(KERNEL_SOURCE[arm])
+    for line in open(TRAFFIC_RECORD):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("arm") != arm:
+            continue
+        if f.get("sha16") != sha:
+            return None, "kernel source changed since the capture"
+        if int(f.get("cts_per_launch", -1)) != int(round(cts_per_launch)):
+            return None, "captured at %s ciphertexts per launch" % f.get("cts_per_launch")
+        return float(f["bytes_per_launch"]), "ncu capture, " + f.get("capture", "")
+    return None, "no record for this kernel"
 
 
 def br_macs(P):
@@ -190,6 +213,98 @@ def synth_pbs_per_image(T):
     return (8 * 12 * 12 + 128 + 10) * T
 
 
+def time_arm(fhe, keys, net, ct, B, variant, steps, warmup, streamed, world, local, flush):
+    """Warm-up, then `steps` timed steps of one variant of the network on
+    device-resident inputs: CUDA events on the launching stream around each
+    step (an L2-flushing write before each, outside the events), nvidia-smi
+    clocks sampled during the timed region, the blind-rotation launches
+    bracketed by their own events for the roofline."""
+    import torch
+    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=not streamed, profile=True)
+    P = keys.params
+    scores = [torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda") for _ in range(2)]
+    stream = torch.cuda.current_stream()
+
+    def one_step(k):
+        if streamed:
+            snn.stream_push(ct, B, scores[k % 2])
+        else:
+            snn.infer(ct, B, scores[0])
+
+    for k in range(warmup):  # streamed: fills the pipeline
+        one_step(k)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    launches0 = fhe.kernel_launches()
+    step_ms, br_ms, br_launches, br_cts = [], 0.0, 0, 0
+    prof0 = snn.profile() if streamed else (0.0, 0, 0)
+    for k in range(steps):
+        flush.zero_()  # L2 flush (256 MiB > 129 MB L2), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step(warmup + k)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if not streamed:
+            ms, nl, nc = snn.profile()
+            br_ms += ms
+            br_launches += nl
+            br_cts += nc
+    barrier(world)
+    launches = fhe.kernel_launches() - launches0
+    clk = clocks.stop()
+    if streamed:
+        ms, nl, nc = snn.profile()
+        br_ms, br_launches, br_cts = ms - prof0[0], nl - prof0[1], nc - prof0[2]
+        snn.stream_flush()  # completes the last batch, after the timed region
+        torch.cuda.synchronize()
+    return {"snn": snn, "total_ms": max_over_ranks(sum(step_ms), world, "cuda"),
+            "br_ms": br_ms, "br_launches": br_launches, "br_cts": br_cts,
+            "launches": int(launches), "clocks": clk, "per_image": snn.pbs_per_image()}
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def roofline(P, arm, res):
+    """Achieved rate of the dominant kernel (blind rotation) from its launch
+    durations measured inside the timed region, against its peak."""
+    br_avg_ms = res["br_ms"] / max(res["br_launches"], 1)
+    cts = res["br_cts"] / max(res["br_launches"], 1)
+    macs_per_launch = br_macs(P) * cts
+    traffic, why = recorded_traffic(arm, cts)
+    if arm == "exact":
+        achieved = macs_per_launch / (br_avg_ms / 1e3) / 1e12
+        peak = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
+                "kernel": "k_blind_rotate_exact<1024,4>",
+                "peak_basis": "152 SMs x 64 INT32 multiply-adds/clk x 2070 MHz (derived)"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        flops = 2.0 * 4 * macs_per_launch  # 4 eight-bit limbs on fp16 tensor cores
+        achieved = flops / (br_avg_ms / 1e3) / 1e12
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "kernel": "k_blind_rotate_tc<1024,4>",
+                "peak_basis": "measured bf16 sustained (fp16 same rate), of measured"}
+    roof["frac"] = achieved / peak
+    roof["traffic"] = traffic
+    roof["traffic_source"] = why
+    roof["launch_ms"] = br_avg_ms
+    roof["launches"] = res["br_launches"]
+    roof["ciphertexts_per_launch"] = cts
+    return roof
+
+
 def run_ours(args):
     import torch
     from paper_2309_09025_gb300 import build, fhe, synth
@@ -199,10 +314,14 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
-    build.build()
+        # replicas load the library built without cluster-multicast copies
+        fhe.use_library(build.build(replica=True))
+    else:
+        build.build()
     P = dict(synth.P630)
     T = 4
     B = args.images
+    streamed = args.schedule == "stream"
     net = synth.csnn_net(T=T)
     # workspace: one bootstrap launch holds every layer's neurons of a batch
     keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, -(-B * 1290 // 256) * 256))
@@ -220,67 +339,21 @@ def run_ours(args):
             probe.free()
         except fhe.FheError:
             pass
-    streamed = args.schedule == "stream"
-    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=not streamed, profile=True)
-    per_image = snn.pbs_per_image()
-    # two score buffers: a streamed batch's scores land during the next push
-    scores = [torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda") for _ in range(2)]
+    arm = "tc" if variant == fhe.VARIANT_TC else "exact"
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def one_step(k):
-        if streamed:
-            snn.stream_push(ct, B, scores[k % 2])
-        else:
-            snn.infer(ct, B, scores[0])
-
-    for k in range(args.warmup):  # streamed: fills the pipeline
-        one_step(k)
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    launches0 = fhe.kernel_launches()
-    step_ms, br_ms, br_launches, br_cts = [], 0.0, 0, 0
-    prof0 = snn.profile() if streamed else (0.0, 0, 0)
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush (256 MiB > 129 MB L2), outside the timed events
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one_step(args.warmup + k)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        if not streamed:
-            ms, nl, nc = snn.profile()
-            br_ms += ms
-            br_launches += nl
-            br_cts += nc
-    barrier()
-    launches = fhe.kernel_launches() - launches0
-    clk = clocks.stop()
-    if streamed:
-        ms, nl, nc = snn.profile()
-        br_ms, br_launches, br_cts = ms - prof0[0], nl - prof0[1], nc - prof0[2]
-        snn.stream_flush()  # completes the last batch, after the timed region
-        torch.cuda.synchronize()
-    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    res = time_arm(fhe, keys, net, ct, B, variant, args.steps, args.warmup, streamed, world,
+                   local, flush)
+    snn, per_image, total_ms = res["snn"], res["per_image"], res["total_ms"]
     value = job_rate(per_image * B * args.steps, world, total_ms)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    if not args.no_e2e and e2e_steps > 0:
         h_in = torch.empty(ct.shape, dtype=torch.int32, pin_memory=True)
         h_in.copy_(ct.cpu())
-        h_out = [torch.empty(scores[0].shape, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        h_out = [torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, pin_memory=True)
+                 for _ in range(2)]
 
         def host_step(k):
             if streamed:
@@ -291,9 +364,9 @@ def run_ours(args):
 
         for k in range(2 if streamed else 1):  # warm the host path (streamed: fill)
             host_step(k)
-        barrier()
+        barrier(world)
         e2e_ms = []
-        for k in range(args.e2e_steps):
+        for k in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -301,35 +374,30 @@ def run_ours(args):
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         if streamed:
             snn.stream_flush()
-        barrier()
+        barrier(world)
         e2e_total = max_over_ranks(sum(e2e_ms), world, "cuda")
-        e2e = {"value": job_rate(per_image * B * args.e2e_steps, world, e2e_total), "unit": UNIT,
+        e2e = {"value": job_rate(per_image * B * e2e_steps, world, e2e_total), "unit": UNIT,
+               "steps": e2e_steps,
                "h2d_bytes_per_step": int(h_in.numel() * 4),
                "d2h_bytes_per_step": int(h_out[0].numel() * 4)}
+    snn.free()
+
+    # the CUDA-core arm of the metric: same workload, schedule and keys
+    exact = None
+    if arm == "tc" and args.exact_steps > 0 and world == 1:
+        xres = time_arm(fhe, keys, net, ct, B, fhe.VARIANT_EXACT, args.exact_steps,
+                        args.exact_warmup, streamed, world, local, flush)
+        xres["snn"].free()
+        xvalue = per_image * B * args.exact_steps / (xres["total_ms"] / 1e3)
+        exact = {"value": xvalue, "unit": UNIT, "steps": args.exact_steps,
+                 "warmup": args.exact_warmup, "ms_per_step": xres["total_ms"] / args.exact_steps,
+                 "ms_per_prediction": xres["total_ms"] / args.exact_steps / B,
+                 "tc_over_exact": value / xvalue,
+                 "roofline": roofline(P, "exact", xres), "clocks": xres["clocks"],
+                 "gpu_launches": xres["launches"]}
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (blind rotation, measured in the timed region)
-    br_avg_ms = br_ms / max(br_launches, 1)
-    macs_per_launch = br_macs(P) * br_cts / max(br_launches, 1)
-    if variant == fhe.VARIANT_EXACT:
-        achieved = macs_per_launch / (br_avg_ms / 1e3) / 1e12
-        peak = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_BYTES["exact"],
-                "kernel": "k_blind_rotate_exact<1024,4>",
-                "peak_basis": "152 SMs x 64 INT32 multiply-adds/clk x 2070 MHz (derived)"}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        flops = 2.0 * 4 * macs_per_launch  # 4 eight-bit limbs on fp16 tensor cores
-        achieved = flops / (br_avg_ms / 1e3) / 1e12
-        peak = float(peaks["bf16_tflops_sustained"])
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_BYTES["tc"],
-                "kernel": "k_blind_rotate_tc<1024, 4>",
-                "peak_basis": "measured bf16 sustained (fp16 same rate), of measured"}
-    roof["launch_ms"] = br_avg_ms
-    roof["launches"] = br_launches
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
@@ -342,7 +410,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_name(P, T, B), "images_per_step": B,
-                   "variant": "tc" if variant == fhe.VARIANT_TC else "exact",
+                   "variant": arm,
                    "schedule": ("streamed: each timed step starts one batch and, in the same "
                                 "bootstrap launches, finishes the batch before it (pipeline "
                                 "filled by the warm-up steps, drained after the timed region); "
@@ -354,11 +422,12 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
         "ms_per_prediction": total_ms / args.steps / B,
         "pbs_per_image": per_image,
-        "roofline": roof,
+        "roofline": roofline(P, arm, res),
+        "exact": exact,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
     }
     print(json.dumps(line), flush=True)
 
@@ -369,13 +438,20 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    # 7 images: a full layer-skewed step is 9030 bootstraps = 71 tiles of 128,
-    # two waves of the 36 co-resident 4-CTA clusters
+    # 7 images: a full layer-skewed iteration bootstraps 7 x 1290 = 9030
+    # ciphertexts = 36 tiles of 256, one wave of the 36 co-resident 4-CTA
+    # clusters
     ap.add_argument("--images", type=int, default=7)
     ap.add_argument("--variant", default="auto", choices=["auto", "exact", "tc"])
     ap.add_argument("--schedule", default="stream", choices=["stream", "batch"],
                     help="stream: batches pipelined across steps; batch: one batch per step")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end-to-end steps (default: --steps)")
+    # the CUDA-core arm is ~10x slower per step: a few steps of the same
+    # workload keep the run within minutes
+    ap.add_argument("--exact-steps", type=int, default=2,
+                    help="timed steps of the CUDA-core arm (0: skip it)")
+    ap.add_argument("--exact-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -12,12 +12,43 @@ number of FFT outputs that decrypt differently from the exact path
 (decryption failures of the FFT product), the number of exact outputs that
 differ from the table value (intrinsic modulus-switch failures of the
 parameter set), and the fraction of FFT outputs bit-identical to the exact
-ones.
+ones.  It also measures the device's FP64 peak (cuBLAS DGEMM through torch,
+best of several 4096^3 products) and reports the FFT blind rotation's FP64
+rate against it: per CMux step, (k+1) l forward and k+1 inverse complex
+transforms of M = N/2 points at 5 M log2 M flops each (the radix-2 count) plus
+(k+1)^2 l M complex multiply-adds of 8 flops.
 """
 import argparse
 import json
 
 import numpy as np
+
+
+def fft_flops_per_pbs(P):
+    """Algorithmic FP64 flops of one FFT blind rotation (n CMux steps)."""
+    import math
+    M, k, l = P["N"] // 2, P["k"], P["l"]
+    transform = 5 * M * math.log2(M)
+    per_step = ((k + 1) * l + (k + 1)) * transform + (k + 1) ** 2 * l * M * 8
+    return P["n"] * per_step
+
+
+def fp64_peak_tflops(n=4096, reps=5):
+    """Measured FP64 rate of cuBLAS DGEMM on this device (TFLOP/s)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def main():
@@ -59,8 +90,13 @@ def main():
         intrinsic += int(np.sum(dec_x != table[m]))
         identical += int(torch.sum(torch.all(out_f == out_x, dim=-1)).item())
         done += b
+    rate = done / (fft_ms / 1e3)
+    flops = fft_flops_per_pbs(P)
+    peak = fp64_peak_tflops()
     print(json.dumps({
-        "params": args.params, "pbs": done, "fft_pbs_per_s": done / (fft_ms / 1e3),
+        "params": args.params, "pbs": done, "fft_pbs_per_s": rate,
+        "fft_fp64_flops_per_pbs": flops, "fft_fp64_tflops": rate * flops / 1e12,
+        "fp64_peak_tflops_measured": peak, "fft_fp64_frac": rate * flops / 1e12 / peak,
         "fft_max_rounding_error": keys.fft_max_error(),
         "fft_decryption_failures_vs_exact": fail,
         "exact_intrinsic_failures": intrinsic,

@@ -5,6 +5,8 @@ identities of paper 2.1 (RGSW product, ACC[-b + sum a_i s_i]) and against the
 closed-form noise of the construction; PBS is brute-forced over every message
 (Thm 2.1: bootstrap(LWE(m)) = LWE(g(m))).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -250,3 +252,34 @@ def test_multi_value_output_noise(oracle_keys):
             scaled.append(float(_signed(int(ph[i]) - exp)) / np.sqrt(var))
     ratio = float(np.var(scaled))
     assert 0.7 < ratio < 1.3, ratio
+
+
+def test_p630_lif_golden_file_starts_with_the_oracles_bootstraps():
+    """The stored P630 LIF hashes (tests/golden/p630_lif_pbs_1000.txt) are
+    the oracle's: its first four entries are recomputed here from the same
+    seeds (keys 2, messages and encryption 6, the LIF pair of 4.2), and the
+    outputs decrypt to the table values of the bootstrap (Thm 2.1)."""
+    import hashlib
+    from paper_2309_09025_gb300 import synth
+    path = os.path.join(os.path.dirname(__file__), "golden", "p630_lif_pbs_1000.txt")
+    golden = [l.split()[1:] for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(golden) == 1000
+    P = dict(synth.P630)
+    p = 1 << P["log2_p"]
+    keys = O.keygen(P, 2)
+    m = synth.uniform_messages(6, 1000, 2 * p)[:4]
+    ct = O.encrypt(P, keys, m, 6)[:4]
+    lif = synth.LIF_DEFAULT
+    luts = O.lif_luts(P, lif["v_th"], lif["leak_shift"], lif["spike_scale"])
+    out = O.pbs(P, keys, ct, luts, nthreads=os.cpu_count())
+    for i in range(4):
+        for j in range(2):
+            h = hashlib.sha256(np.ascontiguousarray(out[j, i], dtype="<u4").tobytes()).hexdigest()[:16]
+            assert h == golden[i][j], (i, j)
+    # decryptions equal f(u) (u < p) or -f(u - p) (negacyclic half) up to a
+    # neighbouring box (the set's modulus-switch failures)
+    for j in range(2):
+        dec = O.decrypt(P, keys, out[j]).astype(np.int64)
+        exp = O.plain_bootstrap(luts[j], m.astype(np.int64), p, centre=False)
+        near = [O.plain_bootstrap(luts[j], m.astype(np.int64) + d, p, centre=False) for d in (-1, 1)]
+        assert np.all((dec == exp) | (dec == near[0]) | (dec == near[1]))
