@@ -325,6 +325,7 @@ def run_ours(args):
     net = synth.csnn_net(T=T)
     # workspace: one bootstrap launch holds every layer's neurons of a batch
     keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, -(-B * 1290 // 256) * 256))
+    keys.set_tc_option(fhe.TC_OPT_L2_HINTS, args.tc_l2_hints)
     images = synth.stroke_images(5 + rank, B)
     ct = fhe.encrypt(keys, images.reshape(-1), seed=11 + rank).view(B, 28 * 28, P["n"] + 1)
     variant = fhe.VARIANT_TC if args.variant == "tc" else fhe.VARIANT_EXACT
@@ -419,6 +420,7 @@ def run_ours(args):
                                "one batch per step: layer-skewed, one bootstrap launch per "
                                "iteration, CUDA graph per iteration",
                    "l2": "256 MiB buffer written before every timed step",
+                   "tc_l2_hints": args.tc_l2_hints,
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
         "ms_per_prediction": total_ms / args.steps / B,
         "pbs_per_image": per_image,
@@ -452,6 +454,9 @@ def main():
     ap.add_argument("--exact-steps", type=int, default=2,
                     help="timed steps of the CUDA-core arm (0: skip it)")
     ap.add_argument("--exact-warmup", type=int, default=1)
+    ap.add_argument("--tc-l2-hints", type=int, default=-1,
+                    help="tensor-core option: L2 evict-last policy on the digit operand "
+                         "(1 on, 0 off, -1 library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -201,17 +201,18 @@ int fhe_pbs_batch_groups(fhe_keys *keys, const uint32_t *ct_in, size_t count, co
 
 /* Autotuner of FHE_VARIANT_AUTO (no counterpart in the paper): times the
  * CUDA-core and tensor-core blind rotations on this device for batches of
- * 128, 256, ... ciphertexts (up to 4096 and the workspace), and stores in the
+ * 16, 32, ... ciphertexts (up to 4096 and the workspace), and stores in the
  * key handle the smallest batch from which the tensor-core path is faster
- * (written to *tc_min_batch; UINT64_MAX when the tensor-core path is not
- * built for these parameters).  Before tuning, AUTO uses tensor cores from
- * 1024 ciphertexts.  It also times the two tile shapes of the tensor-core
- * path (a 256-ciphertext tile on a cluster of 4 or of 8 SMs) at 1, 4 and the
- * most tiles that fit at once in clusters of 8, and keeps clusters of 8 only
- * up to where they were measured no slower (before tuning: whenever the
- * batch fits).  Synchronous; allocates and frees temporary buffers;
- * takes seconds (longest at N = 2048).  Errors: FHE_EINVAL, FHE_ENOMEM,
- * FHE_ECUDA, FHE_ETIMEOUT. */
+ * (1 when it is already faster at 16: a launch below one tile costs one
+ * tile; written to *tc_min_batch; UINT64_MAX when the tensor-core path is not
+ * built for these parameters).  Before tuning, AUTO uses tensor cores for
+ * every batch.  It also times the tile shapes of the tensor-core path (a
+ * 256-ciphertext tile on a cluster of 4, 8 or 16 SMs): each larger shape
+ * against the next smaller one at 1, 4 and the most tiles that fit at once
+ * in the larger shape, keeping the larger one only up to where it was
+ * measured no slower (before tuning: whenever the batch fits).
+ * Synchronous; allocates and frees temporary buffers; takes seconds (longest
+ * at N = 2048).  Errors: FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT. */
 int fhe_pbs_autotune(fhe_keys *keys, uint64_t *tc_min_batch, void *stream);
 
 /* Exactness plan of the tensor-core blind rotation for a parameter set (no
@@ -238,10 +239,31 @@ int fhe_tc_plan_query(const fhe_params *params, fhe_tc_plan *out);
 
 /* What FHE_VARIANT_AUTO and the tensor-core path currently use: the batch
  * size from which AUTO picks tensor cores (UINT64_MAX: never) and the most
- * 256-ciphertext tiles a batch may have to run on clusters of 8 (the device
- * limit before fhe_pbs_autotune; 0: never; -1: the device limit, not yet
- * queried).  Host only.  Errors: FHE_EINVAL. */
-int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles);
+ * 256-ciphertext tiles a batch may have to run on clusters of 8 and of 16
+ * (the device limit before fhe_pbs_autotune; 0: never; -1: the device
+ * limit, not yet queried).  tc_cl16_tiles may be NULL.  Host only.
+ * Errors: FHE_EINVAL. */
+int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles,
+                   int32_t *tc_cl16_tiles);
+
+/* Options of the tensor-core path, for measurements and tuning (no
+ * counterpart in the paper); results are bit-identical under every option.
+ *   FHE_TC_OPT_CLUSTER: 4, 8 or 16 CTAs per 256-ciphertext tile for every
+ *     batch that fits in one wave of that shape (others use clusters of 4),
+ *     or 0 for the tuned rule (16 up to the 16-CTA limit, then 8, then 4).
+ *   FHE_TC_OPT_MULTICAST (clusters of 16 only): 1 = digit tiles copied to
+ *     all CTAs that hold the same rows by cluster-multicast copies, 0 = each
+ *     CTA copies whole tiles, -1 = the build's default (multicast in the
+ *     single-GPU library; the replica library has no multicast and returns
+ *     FHE_EUNSUPPORTED for 1).
+ *   FHE_TC_OPT_L2_HINTS: 1 = the digit operand is stored and copied with an
+ *     L2 evict-last cache policy, 0 = no policy, -1 = the default (none).
+ * Host only; applies from the next call.  Errors: FHE_EINVAL (unknown
+ * option or value), FHE_EUNSUPPORTED. */
+#define FHE_TC_OPT_CLUSTER 0
+#define FHE_TC_OPT_MULTICAST 1
+#define FHE_TC_OPT_L2_HINTS 2
+int fhe_pbs_set_tc_option(fhe_keys *keys, int option, int value);
 
 /* Bootstrapping that allocates nothing (no counterpart in the paper: an
  * integration aid).  Some callers cannot call cudaMalloc at the point where

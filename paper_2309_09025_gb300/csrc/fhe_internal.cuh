@@ -131,8 +131,18 @@ struct fhe_keys {
   // batches of up to this many 256-ciphertext tiles run on clusters of 8
   // (set by fhe_pbs_autotune from timings; -1: up to tc_cl8_max)
   int tc_cl8_tiles;
-  // autotuner only: force clusters of 4 or 8 (0: the rule above)
+  // clusters of 16 CTAs the device holds at once (-1: not queried yet; 0:
+  // none) and the most tiles run on them (-1: up to tc_cl16_max)
+  int tc_cl16_max;
+  int tc_cl16_tiles;
+  // force clusters of 4, 8 or 16 (0: the rules above); set by the autotuner
+  // while it measures and by fhe_pbs_set_tc_shape
   int tc_force_cl;
+  // digit tiles by cluster-multicast copies (1), per CTA (0) or the build's
+  // default (-1: multicast where compiled in)
+  int tc_force_mc;
+  // L2 evict-last policy on the digit operand (1), none (0), default (-1)
+  int tc_l2_hints;
   // tensor-core key layout (built on first use of FHE_VARIANT_TC)
   void *d_bsk_tc;
   size_t bsk_tc_bytes;

@@ -185,11 +185,17 @@ extern "C" int fhe_keygen_from_seed(const fhe_params *prm, uint64_t seed, size_t
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaGetDevice(&K->device) != cudaSuccess) { free(K); return FHE_ECUDA; }
   K->ws_cap = max_batch ? max_batch : 16384;
-  // until fhe_pbs_autotune measures it: tensor cores from four cluster tiles up
-  K->tc_min_batch = fhe::tc_available(P) ? 1024u : SIZE_MAX;
+  // until fhe_pbs_autotune measures it: tensor cores for every batch (a
+  // tensor-core launch of up to 7 tiles runs on 16-CTA clusters, faster than
+  // the CUDA-core path at any size on GB300)
+  K->tc_min_batch = fhe::tc_available(P) ? 1u : SIZE_MAX;
   K->tc_cl8_max = -1;
   K->tc_cl8_tiles = -1;
   K->tc_force_cl = 0;
+  K->tc_cl16_max = -1;
+  K->tc_cl16_tiles = -1;
+  K->tc_force_mc = -1;
+  K->tc_l2_hints = -1;
   const uint64_t bsk_words = (uint64_t)P.n * P.ggsw_words();
   const uint64_t ksk_words = (uint64_t)P.k * P.N * P.l_ks * (P.n + 1u);
   bool ok = cudaMalloc(&K->d_lwe_key, sizeof(uint32_t) * P.n) == cudaSuccess &&

@@ -20,14 +20,18 @@
 // a CTA pair running tcgen05.mma.cta_group::2 with M = 256, N = 256, K = 16:
 //  - A = digits of 256 ciphertexts; each CTA holds its 128 rows in tiles of
 //    128 x 128 (LBO 128, SBO 2048).  Digits are written once per step to
-//    global memory and multicast by cp.async.bulk to the two CTAs (one per
-//    pair) that hold the same 128 rows; each of them sends the 64 rows it
-//    generated.
+//    global memory; each CTA copies the tiles of its 128 rows into shared
+//    memory, either by cluster-multicast bulk copies (single-GPU library:
+//    every CTA sends the rows it generated to all CTAs holding the same rows)
+//    or by whole-tile copies per CTA (replica library, or by option).
 //  - B = Hankel key, N = 256 output coefficients split 128 + 128 between the
 //    two CTAs of the pair.  Core matrix delta holds h[8 delta + rho + kappa];
 //    with LBO = SBO = 128 bytes the matrix descriptor walks one strip of core
 //    matrices for both the N and K directions, so one 10 KB window per
 //    (key row r, limb, 512 K) feeds 32 K16 steps of a 256-coefficient block.
+//    Global memory keeps only the 2N distinct entries h[s] per key
+//    polynomial and limb (4x the key); a producer warp stages the 640 a
+//    window needs and writes the window's core matrices in shared memory.
 //  - D = TMEM fp32, 128 lanes (the CTA's ciphertexts) x 256 columns per
 //    limb; a unit accumulates two limbs, using all 512 columns (allocated
 //    jointly by the pair), so each A tile feeds two MMAs per K16 step.
@@ -35,14 +39,16 @@
 // from shared memory (64 B/clk at the tensor rate) instead of 4 + 8 KB for a
 // single-CTA M128 N256 step.
 //
-// Cluster of 4 CTAs = 2 pairs = 256 ciphertexts.  Pair j computes output
-// polynomial j (all N coefficients, 4 limbs) for all 256 ciphertexts.  Per
-// step: digits (all warps; each CTA makes the digits of 64 ciphertexts) ->
-// cluster barrier -> units (block, limb pair, chunk) run by a digit-tile
-// producer warp, a key-window producer warp, the leader's MMA warp (the
-// peer's warp 1 relays "operand landed" to the leader's barriers) and eight
-// epilogue warps per CTA (TMEM -> registers, limb recombination, ACC update
-// in global memory) -> cluster barrier.
+// A cluster of CL = 4, 8 or 16 CTAs (CL/2 pairs) takes one 256-ciphertext
+// tile; half the pairs compute output polynomial 0, half polynomial 1, each
+// pair a share of the N/256 coefficient blocks (4 CTAs: all blocks, 16 CTAs:
+// one block at N = 1024, the lowest latency).  Per step: digits (all warps;
+// each CTA makes the digits of 256/CL ciphertexts) -> cluster barrier ->
+// units (block, chunk, limb pair) run by a digit-tile producer warp, a
+// key-window warp, the leader's MMA warp (the peer's warp 1 relays "A tile
+// landed" to the leader) and eight epilogue warps per CTA (TMEM ->
+// registers, limb recombination, ACC update in global memory) -> cluster
+// barrier.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -114,6 +120,18 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// Acquire at cluster scope: the phase was completed by another CTA's release
+// arrive after that CTA's threads wrote shared memory with generic stores.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait (two seconds).  Sets *abort and returns false when it gives up;
 // returns false immediately once aborted.
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort) {
@@ -121,6 +139,16 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, vol
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (global_ns() - t0 > 2000000000ull) { *abort = 1; return false; }
+  }
+  return true;
+}
+__device__ __forceinline__ bool wait_bounded_cluster(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (*abort) return false;
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait_cluster(bar, parity)) {
     if (*abort) return false;
     if (global_ns() - t0 > 2000000000ull) { *abort = 1; return false; }
   }
@@ -140,6 +168,30 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+// L2 eviction priority of the digit operand (tc option FHE_TC_OPT_L2_HINTS):
+// a cache policy that makes the lines it touches the last to be evicted.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+// 8-byte global store, with the policy when `hint`.
+__device__ __forceinline__ void st_u2(void *p, uint2 v, bool hint, uint64_t pol) {
+  if (hint)
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "l"(pol)
+                 : "memory");
+  else
+    *reinterpret_cast<uint2 *>(p) = v;
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -183,9 +235,11 @@ __device__ __forceinline__ void tc2_commit_each(uint64_t *bar, uint16_t mask) {
 template <bool MC>
 struct ATileLoad {
   static __device__ __forceinline__ void run(unsigned char *stage, const __half *tile, uint32_t pr,
-                                             uint32_t np, uint64_t *bar, uint16_t mask) {
+                                             uint32_t np, uint64_t *bar, uint16_t mask, bool hint,
+                                             uint64_t pol) {
     (void)pr; (void)np; (void)mask;
-    bulk_g2s(stage, tile, (uint32_t)kATile, bar);
+    if (hint) bulk_g2s_hint(stage, tile, (uint32_t)kATile, bar, pol);
+    else bulk_g2s(stage, tile, (uint32_t)kATile, bar);
   }
 };
 #ifndef FHE_NO_MULTICAST
@@ -197,6 +251,17 @@ __device__ __forceinline__ void tc2_commit_ctas(uint64_t *bar, uint16_t mask) {
   tc2_commit_each(bar, mask);
 }
 #endif
+// Arrive on this CTA's barrier, releasing this thread's prior writes (and
+// those ordered before them) at CTA scope.
+__device__ __forceinline__ void mbar_arrive_local(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Arrive on a barrier of another CTA of the cluster, releasing at cluster
+// scope (the barrier announces generic shared-memory writes of this CTA).
+__device__ __forceinline__ void mbar_arrive_remote_release(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+               : "memory");
+}
 // Arrive on a barrier of another CTA of the cluster (default semantics; the
 // operands it announces were written by the async proxy and are read by the
 // tensor core, which the barrier phase alone orders).
@@ -251,49 +316,52 @@ __device__ __forceinline__ int32_t limb8(uint32_t w, uint32_t L) {
 }
 
 // ---------------------------------------------------------------- key layout
-// strips[((i * R + r) * 2 + j) * 4 + L][delta][rho][kappa] = limb_L(h[8 delta
-// + rho + kappa]), h[s] = ext_{r,j}(s - (N - 1)); 256 core matrices of
-// 8x8 fp16 per strip (the last one is padding).
-__global__ void k_hankel_strips(Params P, const uint32_t *__restrict__ bsk, __half *strips) {
+// hk[((i * R + r) * 2 + j) * 4 + L][s] = limb_L(h[s]) as fp16 for s < 2N,
+// h[s] = ext_{r,j}(s - (N - 1)) (h[2N - 1] = 0): the 2N - 1 distinct entries
+// of the Hankel key matrix of one key polynomial and limb, 4x the size of
+// the key itself.  The kernel builds the 8x8 core matrices of each B window
+// from these in shared memory.
+__global__ void k_hankel_compact(Params P, const uint32_t *__restrict__ bsk, __half *hk) {
   const uint32_t N = P.N, R = P.rows();
-  const uint32_t ncm = N / 4u;  // core matrices per strip
-  const uint64_t rows_total = (uint64_t)P.n * R * 2u * 4u * ncm * 8u;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows_total;
+  const uint64_t total = (uint64_t)P.n * R * 2u * 4u * 2u * N;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t rho = (uint32_t)(e % 8u);
-    const uint32_t delta = (uint32_t)((e / 8u) % ncm);
-    const uint64_t strip = e / (8u * ncm);  // ((i R + r) 2 + j) 4 + L
+    const uint32_t sidx = (uint32_t)(e % (2u * N));
+    const uint64_t strip = e / (2u * N);  // ((i R + r) 2 + j) 4 + L
     const uint32_t L = (uint32_t)(strip % 4u);
-    const uint32_t j = (uint32_t)((strip / 4u) % 2u);
-    const uint64_t ir = strip / 8u;  // i * R + r
-    const uint32_t *K = bsk + (ir * 2u + j) * N;
-    __align__(16) __half row[8];
-    for (uint32_t kap = 0; kap < 8u; ++kap) {
-      const int32_t s = (int32_t)(8u * delta + rho + kap);
-      int32_t v = 0;
-      if (s <= (int32_t)(2u * N - 2u)) {
-        const int32_t x = s - (int32_t)(N - 1u);
-        const uint32_t w = (x >= 0) ? K[x] : (0u - K[x + (int32_t)N]);
-        v = limb8(w, L);
-      }
-      row[kap] = __int2half_rn(v);
+    const uint64_t irj = strip / 4u;      // (i R + r) 2 + j
+    const uint32_t *K = bsk + irj * N;
+    int32_t v = 0;
+    if (sidx <= 2u * N - 2u) {
+      const int32_t x = (int32_t)sidx - (int32_t)(N - 1u);
+      const uint32_t w = (x >= 0) ? K[x] : (0u - K[x + (int32_t)N]);
+      v = limb8(w, L);
     }
-    *reinterpret_cast<uint4 *>(strips + e * 8u) = *reinterpret_cast<const uint4 *>(row);
+    hk[e] = __int2half_rn(v);
   }
 }
 
+// Entries of the compact key one B window reads: core matrices 0..78 of a
+// window span h[s0 .. s0 + 638] (128 columns + K 512 - 1 + 7 + 7); 640 are
+// staged (a 16-byte multiple).
+constexpr uint32_t kHWin = 640u;
+constexpr uint32_t kHStage = kHWin * 2u;  // bytes
+constexpr uint32_t kBCm = 79u;             // core matrices of a window the MMAs read
+
 struct TcSmem {
-  uint32_t a, b, bars, tmem_slot, total;
+  uint32_t a, b, h, bars, tmem_slot, total;
 };
 // A stages, then two B stages of two 128-column windows (one per limb of the
-// unit; each window covers K = 1024).  During the digit phase the A and B
-// regions stage accumulators instead (kGBuf buffers of 32 KB).
+// unit; each window covers K = 512), then the compact key entries staged for
+// each B stage.  During the digit phase the A and B regions stage
+// accumulators instead (kGBuf buffers of 32 KB).
 __host__ __device__ inline TcSmem tc_smem() {
   TcSmem s;
   uint32_t o = 0;
   s.a = o; o += kAStages * kATile;
   s.b = o; o += 2u * 2u * kBWin;
-  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 mbarriers
+  s.h = o; o += 2u * 2u * kHStage;
+  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 + 2 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
@@ -306,17 +374,19 @@ __host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) 
   return 2ull * RR * (N / kKB) * (kATile / 2);
 }
 
-// CL = CTAs per cluster: 4 (two pairs, one per output polynomial) or 8 (four
+// CL = CTAs per cluster: 4 (two pairs, one per output polynomial), 8 (four
 // pairs, each with half the blocks of one polynomial: half the work per CTA
-// and step, for batches that fit in the 15 clusters of 8 the GPU holds).
+// and step) or 16 (eight pairs, a quarter; a non-portable cluster size, for
+// batches that fit in the clusters of 16 the GPU holds at once).  MC: digit
+// tiles by cluster-multicast copies (compiled only into single-GPU builds).
 template <int N, int CL, bool MC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
-    k_blind_rotate_tc(Params P, const __half *__restrict__ strips,
+    k_blind_rotate_tc(Params P, const __half *__restrict__ hk,
                       const uint32_t *__restrict__ ct_in, size_t count,
                       const __grid_constant__ LutArgs lut,
                       uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
                       uint32_t chunk_r, uint32_t sub_shift, uint32_t *__restrict__ big_out,
-                      int *status) {
+                      int *status, uint32_t opts) {
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
   constexpr uint32_t KBLK = N / kKB;             // A tiles per digit row r
   constexpr uint32_t KH = N / kBK;               // B windows per digit row
@@ -331,11 +401,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   const TcSmem S = tc_smem();
   unsigned char *sA = smem + S.a;
   unsigned char *sB = smem + S.b;
+  unsigned char *sH = smem + S.h;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S.bars);
   uint64_t *a_full = bars, *a_empty = bars + kAStages, *a_peer = bars + 2 * kAStages;
   uint64_t *b_full = bars + 3 * kAStages, *b_empty = b_full + 2, *b_peer = b_full + 4;
   uint64_t *t_full = b_full + 6, *t_empty = b_full + 7, *done = b_full + 8;
   uint64_t *g_full = b_full + 9;  // staging buffers of the digit phase
+  uint64_t *h_full = g_full + kGBuf;  // compact key entries of each B stage
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
   __shared__ uint32_t s_abar[RPC];  // a~_i of the ciphertexts whose digits this CTA makes
@@ -363,12 +435,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t nblk = N / kBN / PPJ;        // blocks of 256 output coefficients of this pair
   const uint32_t blk0 = bsub * nblk;
   const uint32_t nchunk = RR / chunk_r;
-  const uint64_t strip_halves = (uint64_t)(N / 4u) * 64u;
+  const uint64_t strip_halves = 2ull * N;  // compact key entries per strip
   const uint16_t pair_mask = (uint16_t)(3u << lead);
   // every CTA of the same half receives the digit rows this CTA makes
   uint16_t a_mask = 0;
   for (uint32_t k = 0; k < NP; ++k) a_mask |= (uint16_t)(1u << (2u * k + hh));
   const uint16_t all_mask = (uint16_t)((1u << CL) - 1u);
+  // opts bit 0: the digit operand is written and copied with an L2
+  // evict-last policy (it is read 2 nblk times per step; the accumulators,
+  // read once and written once per step, are the lines that leave L2)
+  const bool l2keep = (opts & 1u) != 0u;
+  const uint64_t pol_keep = l2keep ? l2_policy_keep() : 0ull;
 
   if (tid == 0) {
     s_abort = 0;
@@ -379,6 +456,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); mbar_init(&b_peer[s], 1);
     }
     for (uint32_t s = 0; s < kGBuf; ++s) mbar_init(&g_full[s], 1);
+    for (int s = 0; s < 2; ++s) mbar_init(&h_full[s], 1);
     mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -535,11 +613,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
               }
             }
             // position tpb + m holds the digit of c0 + 3 - m
-            *reinterpret_cast<uint2 *>(dst0[h] + (uint64_t)r * KBLK * TILE_H) =
-                make_uint2(pack(hv[3], hv[2]), pack(hv[1], hv[0]));
+            st_u2(dst0[h] + (uint64_t)r * KBLK * TILE_H,
+                  make_uint2(pack(hv[3], hv[2]), pack(hv[1], hv[0])), l2keep, pol_keep);
             if (sub_shift != 0u)
-              *reinterpret_cast<uint2 *>(dst0[h] + (uint64_t)(R + r) * KBLK * TILE_H) =
-                  make_uint2(pack(hh2[3], hh2[2]), pack(hh2[1], hh2[0]));
+              st_u2(dst0[h] + (uint64_t)(R + r) * KBLK * TILE_H,
+                    make_uint2(pack(hh2[3], hh2[2]), pack(hh2[1], hh2[0])), l2keep, pol_keep);
           }
         }
       }
@@ -558,37 +636,23 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     asm volatile("fence.proxy.async;" ::: "memory");
     cluster_sync_all();
 
-    // ---- external product units (block, limb pair, chunk) of output
+    // ---- external product units (block, chunk, limb pair) of output
     // polynomial pj: each A tile feeds both limbs of the pair (accumulators
-    // in TMEM columns 0..255 and 256..511).
-    if (warp == 0 || warp == kBWarp) {
-      // producers: warp 0 streams the digit tiles, warp kBWarp the key windows
+    // in TMEM columns 0..255 and 256..511).  The two limb pairs of a chunk
+    // run back to back, so the second pass over the chunk's digit tiles finds
+    // them in L2.
+    if (warp == 0) {
+      // digit-tile producer
       if (lane == 0) {
         // per-CTA tile copies also read the rows other CTAs generated (their
         // generic stores were fenced for the async proxy before the barrier)
         if (!MC) asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
-          const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
-          for (uint32_t lp = 0; lp < 2u; ++lp)
-            for (uint32_t ch = 0; ch < nchunk; ++ch)
+        for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
+          for (uint32_t ch = 0; ch < nchunk; ++ch)
+            for (uint32_t lp = 0; lp < 2u; ++lp)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t r = ch * chunk_r + rr;
-                  if (warp == kBWarp) {
-                    const uint32_t bs = b_it & 1u;
-                    if (b_it >= 2u) wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
-                    if (!s_abort) {
-                      mbar_expect_tx(&b_full[bs], 2u * kBWin);
-                      for (uint32_t z = 0; z < 2u; ++z) {
-                        const __half *src = strips +
-                                            ((((uint64_t)i * R + r % R) * 2u + pj) * 4u + 2u * lp + z) * strip_halves +
-                                            (uint64_t)((c0 + kBK * kh) / 8u) * 64u;
-                        bulk_g2s(sB + (bs * 2u + z) * kBWin, src, kBWin, &b_full[bs]);
-                      }
-                    }
-                    ++b_it;
-                    continue;
-                  }
                   for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     if (a_it >= kAStages)
@@ -596,19 +660,87 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!s_abort) {
                       const __half *tsrc = dig_h + (uint64_t)(r * KBLK + KT * kh + kb) * TILE_H;
                       mbar_expect_tx(&a_full[as], kATile);
-                      ATileLoad<MC>::run(sA + as * kATile, tsrc, pr, NP, &a_full[as], a_mask);
+                      ATileLoad<MC>::run(sA + as * kATile, tsrc, pr, NP, &a_full[as], a_mask,
+                                         l2keep, pol_keep);
                     }
                     ++a_it;
                   }
                 }
-        }
+      }
+      __syncwarp();
+    } else if (warp == kBWarp) {
+      // key-window producer: per window, the 640 compact entries of both
+      // limbs are staged by bulk copies and the warp writes the window's 79
+      // core matrices (row rho of core matrix d = entries s0 + 8 d + rho ..
+      // + 7; lanes 8g .. 8g + 7 write the 8 rows of one core matrix, 128
+      // contiguous bytes).  Generic stores: each lane fences them for the
+      // tensor core (async proxy); then the leader's window is announced on
+      // its b_full (release, CTA scope) and the peer's on the leader's b_peer
+      // (release, cluster scope).
+      const uint32_t g = lane >> 3, rho = lane & 7u;
+      const bool odd = (rho & 1u) != 0u;
+      for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
+        const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
+        for (uint32_t ch = 0; ch < nchunk; ++ch)
+          for (uint32_t lp = 0; lp < 2u; ++lp)
+            for (uint32_t rr = 0; rr < chunk_r; ++rr)
+              for (uint32_t kh = 0; kh < KH; ++kh) {
+                const uint32_t r = ch * chunk_r + rr;
+                const uint32_t bs = b_it & 1u;
+                bool go = true;
+                if (b_it >= 2u) go = wait_bounded(&b_empty[bs], ((b_it >> 1) - 1u) & 1u, &s_abort);
+                go = __all_sync(0xffffffffu, go && !s_abort);
+                unsigned char *hst = sH + bs * 2u * kHStage;
+                if (go && lane == 0) {
+                  // earlier generic reads of this staging buffer precede the copies
+                  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                  mbar_expect_tx(&h_full[bs], 2u * kHStage);
+                  const uint32_t s0 = c0 + kBK * kh;
+                  for (uint32_t z = 0; z < 2u; ++z) {
+                    const __half *src =
+                        hk + ((((uint64_t)i * R + r % R) * 2u + pj) * 4u + 2u * lp + z) * strip_halves + s0;
+                    bulk_g2s(hst + z * kHStage, src, kHStage, &h_full[bs]);
+                  }
+                }
+                __syncwarp();
+                if (go) go = __all_sync(0xffffffffu, wait_bounded(&h_full[bs], (b_it >> 1) & 1u, &s_abort));
+                if (go) {
+#pragma unroll
+                  for (uint32_t z = 0; z < 2u; ++z) {
+                    const uint32_t *hw = reinterpret_cast<const uint32_t *>(hst + z * kHStage);
+                    unsigned char *win = sB + (bs * 2u + z) * kBWin;
+#pragma unroll 4
+                    for (uint32_t d0 = 0; d0 < kBCm; d0 += 4u) {
+                      const uint32_t d = d0 + g;
+                      if (d < kBCm) {
+                        // entries 8d + rho .. + 7 = halves rho .. rho + 7 of words 4d ..
+                        const uint32_t *w = hw + 4u * d + (rho >> 1);
+                        const uint32_t x0 = w[0], x1 = w[1], x2 = w[2], x3 = w[3], x4 = w[4];
+                        uint4 o;
+                        o.x = odd ? __funnelshift_r(x0, x1, 16) : x0;
+                        o.y = odd ? __funnelshift_r(x1, x2, 16) : x1;
+                        o.z = odd ? __funnelshift_r(x2, x3, 16) : x2;
+                        o.w = odd ? __funnelshift_r(x3, x4, 16) : x3;
+                        *reinterpret_cast<uint4 *>(win + d * 128u + rho * 16u) = o;
+                      }
+                    }
+                  }
+                  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                  __syncwarp();
+                  if (lane == 0) {
+                    if (leader) mbar_arrive_local(&b_full[bs]);
+                    else mbar_arrive_remote_release(cluster_addr(&b_peer[bs], lead));
+                  }
+                }
+                ++b_it;
+              }
       }
       __syncwarp();
     } else if (warp == 1) {
       if (lane == 0 && leader) {
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
-          for (uint32_t lp = 0; lp < 2u; ++lp)
-            for (uint32_t ch = 0; ch < nchunk; ++ch) {
+          for (uint32_t ch = 0; ch < nchunk; ++ch)
+            for (uint32_t lp = 0; lp < 2u; ++lp) {
               if (u_it >= 1u) wait_bounded(t_empty, (u_it - 1u) & 1u, &s_abort);
               tc_fence_after();
               uint32_t accum = 0;
@@ -616,7 +748,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t bs = b_it & 1u;
                   wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort);
-                  wait_bounded(&b_peer[bs], (b_it >> 1) & 1u, &s_abort);
+                  wait_bounded_cluster(&b_peer[bs], (b_it >> 1) & 1u, &s_abort);
+                  tc_fence_after();
                   const uint32_t bbase = smem_u32(sB + bs * 2u * kBWin);
                   for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
@@ -647,17 +780,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
               ++u_it;
             }
       } else if (lane == 0) {
-        // peer: tell the leader when this CTA's halves of A and B have landed
-        const uint32_t bp0 = cluster_addr(&b_peer[0], lead), bp1 = cluster_addr(&b_peer[1], lead);
+        // peer: tell the leader when this CTA's half of each A tile has landed
+        // (its B windows are announced by its key-window warp)
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
-          for (uint32_t lp = 0; lp < 2u; ++lp)
-            for (uint32_t ch = 0; ch < nchunk; ++ch)
+          for (uint32_t ch = 0; ch < nchunk; ++ch)
+            for (uint32_t lp = 0; lp < 2u; ++lp)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
-                  const uint32_t bs = b_it & 1u;
-                  if (wait_bounded(&b_full[bs], (b_it >> 1) & 1u, &s_abort))
-                    mbar_arrive_remote(bs ? bp1 : bp0);
-                  ++b_it;
                   for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     if (wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort))
@@ -682,8 +811,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
           const uint4 v = *reinterpret_cast<const uint4 *>(dst + k);
           outv[k] = v.x; outv[k + 1] = v.y; outv[k + 2] = v.z; outv[k + 3] = v.w;
         }
-        for (uint32_t lp = 0; lp < 2u; ++lp)
-          for (uint32_t ch = 0; ch < nchunk; ++ch) {
+        for (uint32_t ch = 0; ch < nchunk; ++ch)
+          for (uint32_t lp = 0; lp < 2u; ++lp) {
             const uint32_t sub = (ch * chunk_r >= R) ? sub_shift : 0u;
             const bool got = wait_bounded(t_full, u_it & 1u, &s_abort);
             const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
@@ -811,8 +940,9 @@ static uint32_t tc_digit_rows(const Params &P) { return tc_sub_shift(P) ? 2u * P
 int tc_prepare(fhe_keys *K) {
   const Params &P = K->P;
   if (K->d_bsk_tc && K->d_acc_tc && K->d_digits_tc) return FHE_OK;
+  // compact Hankel key: 2N fp16 per (key row, polynomial, limb)
   const uint64_t strips = (uint64_t)P.n * P.rows() * 2u * 4u;
-  K->bsk_tc_bytes = strips * (P.N / 4u) * 128u;
+  K->bsk_tc_bytes = strips * 2u * P.N * sizeof(__half);
   const uint64_t tiles = (K->ws_cap + kBt - 1) / kBt;
   if (cudaMalloc(&K->d_bsk_tc, K->bsk_tc_bytes) != cudaSuccess) return FHE_ENOMEM;
   if (cudaMalloc(&K->d_acc_tc, sizeof(uint32_t) * tiles * tc_tile_acc_words(P.N)) != cudaSuccess)
@@ -820,7 +950,7 @@ int tc_prepare(fhe_keys *K) {
   if (cudaMalloc(&K->d_digits_tc, sizeof(__half) * tiles * tc_tile_dig_halves(P.N, tc_digit_rows(P))) !=
       cudaSuccess)
     return FHE_ENOMEM;
-  k_hankel_strips<<<152u * 16u, 256>>>(P, K->d_bsk, (__half *)K->d_bsk_tc);
+  k_hankel_compact<<<152u * 16u, 256>>>(P, K->d_bsk, (__half *)K->d_bsk_tc);
   note_launches(1);
   FHE_CUDA_TRY(cudaGetLastError());
   FHE_CUDA_TRY(cudaDeviceSynchronize());
@@ -837,6 +967,43 @@ int pbs_prepare(fhe_keys *K, int variant) {
   return tc_prepare(K);
 }
 
+using TcKernel = decltype(&k_blind_rotate_tc<1024, 4, false>);
+
+// Instance of the blind rotation for ring size N, cluster size cl (4, 8 or
+// 16 CTAs per 256-ciphertext tile) and digit-tile copy form.  The single-GPU
+// build compiles multicast instances for every cluster size and per-CTA ones
+// for clusters of 16; the replica build only per-CTA ones.
+template <int N>
+static TcKernel tc_kernel(int cl, bool mc) {
+#ifndef FHE_NO_MULTICAST
+  if (mc) return cl == 16 ? k_blind_rotate_tc<N, 16, true>
+                          : (cl == 8 ? k_blind_rotate_tc<N, 8, true> : k_blind_rotate_tc<N, 4, true>);
+  if (cl == 16) return k_blind_rotate_tc<N, 16, false>;
+  return nullptr;
+#else
+  (void)mc;
+  return cl == 16 ? k_blind_rotate_tc<N, 16, false>
+                  : (cl == 8 ? k_blind_rotate_tc<N, 8, false> : k_blind_rotate_tc<N, 4, false>);
+#endif
+}
+
+// Clusters of `cl` CTAs of `kern` the device holds at once (0 when the
+// shape cannot launch, e.g. a 16-CTA cluster where the device does not
+// allow that non-portable size).
+static int tc_max_clusters(TcKernel kern, int cl, uint32_t smem) {
+  if (cl > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) { (void)cudaGetLastError(); n = 0; }
+  return n;
+}
+
 int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
            uint32_t *ct_out, size_t table_stride, cudaStream_t st, const uint64_t *seg_end) {
   const Params &P = K->P;
@@ -845,35 +1012,51 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   if (rc) return rc;
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem();
-  auto kern4 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 4, kTcMulticast> : k_blind_rotate_tc<2048, 4, kTcMulticast>;
-  auto kern8 = (P.N == 1024u) ? k_blind_rotate_tc<1024, 8, kTcMulticast> : k_blind_rotate_tc<2048, 8, kTcMulticast>;
-  FHE_CUDA_TRY(cudaFuncSetAttribute(kern4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
-  FHE_CUDA_TRY(cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
-  if (K->tc_cl8_max < 0) {  // clusters of 8 the device holds at once (once per key handle)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(8);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = S.total;
-    int n8 = 0;
-    if (cudaOccupancyMaxActiveClusters(&n8, kern8, &cfg) != cudaSuccess) { (void)cudaGetLastError(); n8 = 0; }
-    K->tc_cl8_max = n8;
+  auto pick = [&](int cl, bool mc) { return P.N == 1024u ? tc_kernel<1024>(cl, mc) : tc_kernel<2048>(cl, mc); };
+  // clusters of 4 and 8 copy digit tiles as the build does; clusters of 16
+  // may be switched to per-CTA copies (fhe_pbs_set_tc_shape)
+  const bool mc16 = (K->tc_force_mc < 0 || !kTcMulticast) ? kTcMulticast : (K->tc_force_mc != 0);
+  TcKernel k4 = pick(4, kTcMulticast), k8 = pick(8, kTcMulticast), k16 = pick(16, mc16);
+  for (TcKernel k : {k4, k8, k16})
+    FHE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  // 16 CTAs per cluster is a non-portable size (where refused, the occupancy
+  // query below reports no such clusters and the shape is never used)
+  if (cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    K->tc_cl16_max = 0;
   }
+  // clusters of 8 and 16 the device holds at once (once per key handle)
+  if (K->tc_cl8_max < 0) K->tc_cl8_max = tc_max_clusters(k8, 8, S.total);
+  if (K->tc_cl16_max < 0) K->tc_cl16_max = tc_max_clusters(k16, 16, S.total);
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
     const LutArgs la = lut_args(lut, seg_end, s0);
-    const unsigned tiles = (unsigned)((cnt + kBt - 1) / kBt);
-    // a batch that fits in one wave of 8-CTA clusters runs with half the work
-    // per CTA and step (lower latency); larger ones use the 36 clusters of 4.
-    // The autotuner may lower the limit where it measured clusters of 4 faster.
-    const int limit = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
-                                                                               : K->tc_cl8_max;
-    const bool eight = K->tc_force_cl ? (K->tc_force_cl == 8 && (int)tiles <= K->tc_cl8_max)
-                                      : (int)tiles <= limit;
+    const int tiles = (int)((cnt + kBt - 1) / kBt);
+    // A batch that fits in one wave of 16-CTA clusters runs on them (a
+    // quarter of the work per CTA and step of the 4-CTA shape: the lowest
+    // latency), one that fits in a wave of 8-CTA clusters on those, larger
+    // ones on the 36 clusters of 4.  The autotuner may lower both limits
+    // where it measured the smaller shape faster.
+    const int lim16 = (K->tc_cl16_tiles >= 0 && K->tc_cl16_tiles < K->tc_cl16_max) ? K->tc_cl16_tiles
+                                                                                 : K->tc_cl16_max;
+    const int lim8 = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
+                                                                            : K->tc_cl8_max;
+    int cl = 4;
+    if (K->tc_force_cl) {
+      if (K->tc_force_cl == 16 && tiles <= K->tc_cl16_max) cl = 16;
+      else if (K->tc_force_cl == 8 && tiles <= K->tc_cl8_max) cl = 8;
+    } else if (tiles <= lim16) {
+      cl = 16;
+    } else if (tiles <= lim8) {
+      cl = 8;
+    }
+    TcKernel kern = (cl == 16) ? k16 : (cl == 8 ? k8 : k4);
     const bool prof = (s0 == 0) && K->prof_ev0;
     if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
-    (eight ? kern8 : kern4)<<<tiles * (eight ? 8u : 4u), kThreads, S.total, st>>>(
+    kern<<<(unsigned)tiles * (unsigned)cl, kThreads, S.total, st>>>(
         P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
-        (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status);
+        (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status,
+        K->tc_l2_hints > 0 ? 1u : 0u);
     note_launches(1);
     FHE_CUDA_TRY(cudaGetLastError());
     if (prof) FHE_CUDA_TRY(record_prof_event(K->prof_ev1, st));
@@ -919,7 +1102,12 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
             cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   size_t best = SIZE_MAX;
   int wins = 0;
-  for (size_t c = 128; ok && rc == FHE_OK && c <= cmax; c *= 2) {
+  // Below one tile the tensor-core launch takes the latency of one tile (on
+  // a cluster of 16 about a third of a CUDA-core launch of even 4
+  // ciphertexts), so sampling starts at 16 ciphertexts; a tensor-core win
+  // there holds for every smaller batch.
+  const size_t c_first = 16;
+  for (size_t c = c_first; ok && rc == FHE_OK && c <= cmax; c *= 2) {
     float t[2] = {0.f, 0.f};
     for (int v = 0; v < 2 && rc == FHE_OK; ++v) {
       const int variant = v ? FHE_VARIANT_TC : FHE_VARIANT_EXACT;
@@ -939,27 +1127,26 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
       wins = 0;
     }
   }
-  // cluster shape of the tensor-core tiles: a batch of t tiles (t up to the
-  // clusters of 8 the device holds) runs on t clusters of 8 (half the work
-  // per CTA and step) or t clusters of 4; time both at t = 1, 4 and the
-  // largest t, and keep clusters of 8 up to the largest sampled t at and
-  // below which they were never slower
-  int cl8_tiles = -1;
-  if (ok && rc == FHE_OK && K->tc_cl8_max > 0 && cmax >= 256u) {
+  // cluster shape of the tensor-core tiles: a batch of t tiles that fits in
+  // one wave of the larger shape runs on t clusters of 8 (half the work per
+  // CTA and step of clusters of 4) or of 16 (a quarter); time each larger
+  // shape against the next smaller one at t = 1, 4 and its largest t, and
+  // keep it up to the largest sampled t at and below which it was never slower
+  auto tune_shape = [&](int small, int large, int max_large) {
     std::vector<int> samples;  // 1, 4 and the largest t, those that fit
-    for (int t : {1, 4, K->tc_cl8_max})
-      if (t <= K->tc_cl8_max && (size_t)t * 256u <= cmax && (samples.empty() || t > samples.back()))
+    for (int t : {1, 4, max_large})
+      if (t <= max_large && (size_t)t * 256u <= cmax && (samples.empty() || t > samples.back()))
         samples.push_back(t);
-    cl8_tiles = 0;
+    int keep = 0;
     for (int v = 0; v < 2 && rc == FHE_OK; ++v) {  // warm both instances
-      K->tc_force_cl = v ? 8 : 4;
+      K->tc_force_cl = v ? large : small;
       rc = fhe::pbs_run(K, d_in, 256u, lut, d_out, 256u * W, FHE_VARIANT_TC, st);
     }
     for (size_t si = 0; si < samples.size() && ok && rc == FHE_OK; ++si) {
       const size_t c = (size_t)samples[si] * 256u;
       float t[2] = {0.f, 0.f};
       for (int v = 0; v < 2 && ok && rc == FHE_OK; ++v) {
-        K->tc_force_cl = v ? 8 : 4;
+        K->tc_force_cl = v ? large : small;
         ok = cudaEventRecord(e0, st) == cudaSuccess;
         rc = fhe::pbs_run(K, d_in, c, lut, d_out, c * W, FHE_VARIANT_TC, st);
         ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
@@ -967,10 +1154,15 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
       }
       if (!ok || rc) break;
       if (t[1] > t[0]) break;
-      cl8_tiles = samples[si];
+      keep = samples[si];
     }
     K->tc_force_cl = 0;
-  }
+    return keep;
+  };
+  int cl8_tiles = -1, cl16_tiles = -1;
+  if (ok && rc == FHE_OK && K->tc_cl8_max > 0 && cmax >= 256u) cl8_tiles = tune_shape(4, 8, K->tc_cl8_max);
+  if (ok && rc == FHE_OK && K->tc_cl16_max > 0 && cmax >= 256u)
+    cl16_tiles = tune_shape(K->tc_cl8_max > 0 ? 8 : 4, 16, K->tc_cl16_max);
   if (!ok && rc == FHE_OK) { (void)cudaGetLastError(); rc = FHE_ECUDA; }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -979,18 +1171,44 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
   fhe_lut_free(lut);
   if (rc) return rc;
   K->tc_cl8_tiles = cl8_tiles;
+  K->tc_cl16_tiles = cl16_tiles;
   // tensor cores never won up to cmax: use them only above it
-  K->tc_min_batch = (best == SIZE_MAX) ? 2 * cmax : best;
+  K->tc_min_batch = (best == SIZE_MAX) ? 2 * cmax : (best == c_first ? 1u : best);
   *tc_min_batch = K->tc_min_batch;
   return fhe_status(K, stream);
 }
 
-extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles) {
+extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles,
+                              int32_t *tc_cl16_tiles) {
   if (!K || !tc_min_batch || !tc_cl8_tiles) return FHE_EINVAL;
   *tc_min_batch = (K->tc_min_batch == SIZE_MAX) ? UINT64_MAX : (uint64_t)K->tc_min_batch;
   *tc_cl8_tiles = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
                                                                            : K->tc_cl8_max;
+  if (tc_cl16_tiles)
+    *tc_cl16_tiles = (K->tc_cl16_tiles >= 0 && K->tc_cl16_tiles < K->tc_cl16_max) ? K->tc_cl16_tiles
+                                                                                 : K->tc_cl16_max;
   return FHE_OK;
+}
+
+extern "C" int fhe_pbs_set_tc_option(fhe_keys *K, int option, int value) {
+  if (!K) return FHE_EINVAL;
+  switch (option) {
+    case FHE_TC_OPT_CLUSTER:
+      if (value != 0 && value != 4 && value != 8 && value != 16) return FHE_EINVAL;
+      K->tc_force_cl = value;
+      return FHE_OK;
+    case FHE_TC_OPT_MULTICAST:
+      if (value < -1 || value > 1) return FHE_EINVAL;
+      if (value == 1 && !kTcMulticast) return FHE_EUNSUPPORTED;
+      K->tc_force_mc = value;
+      return FHE_OK;
+    case FHE_TC_OPT_L2_HINTS:
+      if (value < -1 || value > 1) return FHE_EINVAL;
+      K->tc_l2_hints = value;
+      return FHE_OK;
+    default:
+      return FHE_EINVAL;
+  }
 }
 
 extern "C" int fhe_tc_plan_query(const fhe_params *params, fhe_tc_plan *out) {

@@ -29,11 +29,24 @@ __device__ __forceinline__ void bulk_g2s_multicast(void *dst, const void *src, u
 // Each of the np CTAs holding the same 128 rows sends the rows it generated
 // (share pr of the tile) to all of them; the tile is complete in every CTA
 // once all np shares have landed (kATile bytes on each CTA's barrier).
+__device__ __forceinline__ void bulk_g2s_multicast_hint(void *dst, const void *src, uint32_t bytes,
+                                                        uint64_t *bar, uint16_t mask, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      ".L2::cache_hint [%0], [%1], %2, [%3], %4, %5;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask), "l"(pol)
+      : "memory");
+}
+
 template <>
 struct ATileLoad<true> {
   static __device__ __forceinline__ void run(unsigned char *stage, const __half *tile, uint32_t pr,
-                                             uint32_t np, uint64_t *bar, uint16_t mask) {
+                                             uint32_t np, uint64_t *bar, uint16_t mask, bool hint,
+                                             uint64_t pol) {
     const uint32_t share = (uint32_t)kATile / np;  // bytes
-    bulk_g2s_multicast(stage + pr * share, tile + pr * (share / 2u), share, bar, mask);
+    if (hint)
+      bulk_g2s_multicast_hint(stage + pr * share, tile + pr * (share / 2u), share, bar, mask, pol);
+    else
+      bulk_g2s_multicast(stage + pr * share, tile + pr * (share / 2u), share, bar, mask);
   }
 };

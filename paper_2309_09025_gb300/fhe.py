@@ -29,6 +29,7 @@ LAYER_FC, LAYER_CONV, LAYER_POISSON = 0, 1, 2
 LIF_MULTI_VALUE, LIF_TWO_PBS = 0, 1
 SNN_PROFILE = 2
 STATE_SPIKES, STATE_MEMBRANES, STATE_CURRENTS = 0, 1, 2
+TC_OPT_CLUSTER, TC_OPT_MULTICAST, TC_OPT_L2_HINTS = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = (
@@ -42,6 +43,7 @@ EXPORTED = (
     "fhe_snn_stream_push", "fhe_snn_stream_flush", "fhe_pbs_autotune",
     "fhe_lut_create_spaces", "fhe_pbs_batch_groups", "fhe_pbs_tuning", "fhe_tc_plan_query",
     "fhe_snn_stream_stage", "fhe_snn_stream_iterate", "fhe_snn_stream_state",
+    "fhe_pbs_set_tc_option",
 )
 LUT_MAX_GROUPS = 8
 PBS_NOALLOC_MAX_WORDS = 1 << 20
@@ -155,7 +157,9 @@ def lib():
             "fhe_pbs_autotune": (ctypes.c_int, [vp, ctypes.POINTER(u64), vp]),
             "fhe_lut_create_spaces": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(vp)]),
             "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
-            "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32)]),
+            "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i32)]),
+            "fhe_pbs_set_tc_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
             "fhe_tc_plan_query": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(TcPlan)]),
             "fhe_snn_stream_stage": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
             "fhe_snn_stream_iterate": (ctypes.c_int, [vp, vp]),
@@ -257,10 +261,17 @@ class Keys:
 
     def tuning(self):
         """fhe_pbs_tuning: (smallest batch AUTO runs on tensor cores or None,
-        most tiles run on clusters of 8)."""
-        v, c = ctypes.c_uint64(), ctypes.c_int32()
-        _check(lib().fhe_pbs_tuning(self.handle, ctypes.byref(v), ctypes.byref(c)), "pbs_tuning")
-        return (None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value)
+        most tiles run on clusters of 8, most tiles run on clusters of 16)."""
+        v, c, c16 = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fhe_pbs_tuning(self.handle, ctypes.byref(v), ctypes.byref(c),
+                                    ctypes.byref(c16)), "pbs_tuning")
+        return (None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value), int(c16.value)
+
+    def set_tc_option(self, option, value):
+        """fhe_pbs_set_tc_option: TC_OPT_CLUSTER (0, 4, 8, 16),
+        TC_OPT_MULTICAST (-1, 0, 1) or TC_OPT_L2_HINTS (-1, 0, 1)."""
+        _check(lib().fhe_pbs_set_tc_option(self.handle, int(option), int(value)),
+               "pbs_set_tc_option")
 
 
 def tc_plan(params):

@@ -2,6 +2,8 @@
 
     python -m paper_2309_09025_gb300.sweep [--params P630] [--batches 256,1024,4096,16384,65536]
                                            [--variants exact,tc,fft,auto] [--reps 3]
+                                           [--tc-cluster 0|4|8|16] [--tc-multicast -1|0|1]
+                                           [--tc-l2-hints -1|0|1]
 
 Uniform random messages of Z_64 bootstrapped with the identity-plus-threshold
 table f(u) = (u + [u >= p/2]) mod p through fhe_pbs_batch; the ciphertexts
@@ -26,6 +28,12 @@ def main():
     ap.add_argument("--variants", default="exact,tc")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--tc-cluster", type=int, default=0,
+                    help="tensor-core tile shape: 4, 8 or 16 CTAs per tile (0: tuned rule)")
+    ap.add_argument("--tc-multicast", type=int, default=-1,
+                    help="clusters of 16: 1 multicast, 0 per-CTA digit-tile copies, -1 default")
+    ap.add_argument("--tc-l2-hints", type=int, default=-1,
+                    help="1: L2 evict-last policy on the digit operand, 0: none, -1: default")
     args = ap.parse_args()
     build.build()
     P = dict(synth.PRESETS[args.params])
@@ -34,6 +42,9 @@ def main():
     # workspace for the largest batch, so that no batch is split into chunks
     keys = fhe.keygen_from_seed(P, seed=args.seed, max_batch=max(16384, -(-max(batches) // 256) * 256))
     lut = fhe.lut_create(keys, synth.identity_plus_threshold_lut(p)[None])
+    keys.set_tc_option(fhe.TC_OPT_CLUSTER, args.tc_cluster)
+    keys.set_tc_option(fhe.TC_OPT_MULTICAST, args.tc_multicast)
+    keys.set_tc_option(fhe.TC_OPT_L2_HINTS, args.tc_l2_hints)
     macs = P["n"] * (P["k"] + 1) ** 2 * P["l"] * P["N"] ** 2
     for variant in args.variants.split(","):
         v = {"exact": fhe.VARIANT_EXACT, "tc": fhe.VARIANT_TC, "fft": fhe.VARIANT_FFT,
@@ -64,6 +75,8 @@ def main():
             dec = fhe.decrypt(keys, out[0]).cpu().numpy()
             exact = float(np.mean(dec % (2 * p) == synth.identity_plus_threshold_lut(p)[msgs]))
             print(json.dumps({"params": args.params, "variant": variant, "batch": batch,
+                              "tc_cluster": args.tc_cluster, "tc_multicast": args.tc_multicast,
+                              "tc_l2_hints": args.tc_l2_hints,
                               "ms": ms, "pbs_per_s": batch / (ms / 1e3),
                               "br_tmac_per_s": macs * batch / (ms / 1e3) / 1e12,
                               "decrypt_exact_fraction": exact}), flush=True)

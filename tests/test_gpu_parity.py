@@ -240,8 +240,10 @@ def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
     """Tensor-core blind rotation: every output of a multi-cluster batch
     (ragged against 256-ciphertext cluster tiles) bit-identical to the
     CUDA-core path, outputs at the tile edges bit-identical to the oracle, for
-    both table counts (P750: N = 2048 with split sub-digits).  Up to 15 tiles
-    run on clusters of 8 CTAs, 16 tiles (3999 ciphertexts) on clusters of 4."""
+    both table counts (P750: N = 2048 with split sub-digits).  With the
+    default rule, the small batches run on clusters of 16 CTAs and 16 tiles
+    (3999 ciphertexts) on clusters of 4 (every shape is forced in
+    test_tc_every_tile_shape_bit_exact)."""
     P, K = gpu_keys(fhe, name, 3)
     _, OK = oracle_keys(name, 3)
     p = 1 << P["log2_p"]
@@ -256,6 +258,39 @@ def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
         idx = np.array([0, 255, 256, count - 1])
         ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
         assert np.array_equal(got[:, idx], ref)
+    assert K.status() == fhe.FHE_OK
+
+
+@pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 613)])
+def test_tc_every_tile_shape_bit_exact(fhe, oracle_keys, name, count):
+    """Every shape of the tensor-core kernel forced in turn (fhe_pbs_set_tc_option):
+    256-ciphertext tiles on clusters of 4, 8 and 16 CTAs, the 16-CTA shape
+    with multicast and with per-CTA digit-tile copies, with and without the
+    L2 policy on the digit operand; all outputs of both
+    LIF tables bit-identical to the CUDA-core path, tile-edge outputs to the
+    oracle."""
+    P, K = gpu_keys(fhe, name, 3)
+    _, OK = oracle_keys(name, 3)
+    p = 1 << P["log2_p"]
+    m = synth.uniform_messages(47, count, 2 * p)
+    ct = fhe.encrypt(K, m, seed=23)
+    luts = _luts(P, 2)
+    lut = fhe.lut_create(K, luts)
+    ref_gpu = u32(fhe.pbs_batch(K, ct, lut, fhe.VARIANT_EXACT))
+    idx = np.array([0, 255, 256, count - 1])
+    ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
+    assert np.array_equal(ref_gpu[:, idx], ref)
+    try:
+        for cluster, mc, hint in [(4, -1, 0), (8, -1, 0), (16, 1, 0), (16, 0, 0), (4, -1, 1),
+                                  (16, 1, 1)]:
+            K.set_tc_option(fhe.TC_OPT_CLUSTER, cluster)
+            K.set_tc_option(fhe.TC_OPT_MULTICAST, mc)
+            K.set_tc_option(fhe.TC_OPT_L2_HINTS, hint)
+            got = u32(pbs(fhe, K, ct, lut, "TC"))
+            assert np.array_equal(got, ref_gpu), f"clusters of {cluster}, multicast {mc}, L2 {hint}"
+    finally:
+        for opt, v in ((fhe.TC_OPT_CLUSTER, 0), (fhe.TC_OPT_MULTICAST, -1), (fhe.TC_OPT_L2_HINTS, -1)):
+            K.set_tc_option(opt, v)
     assert K.status() == fhe.FHE_OK
 
 
@@ -396,15 +431,16 @@ def test_autotuned_variant_is_bit_exact(fhe, oracle_keys, name):
     P, K = gpu_keys(fhe, name, 3)
     p = 1 << P["log2_p"]
     cross = K.autotune()
-    tuned, cl8_tiles = K.tuning()
+    tuned, cl8_tiles, cl16_tiles = K.tuning()
     assert tuned == cross
     if name == "P64":
         assert cross is None
     else:
-        assert cross is not None and 128 <= cross <= 8192
+        assert cross is not None and 1 <= cross <= 8192
         assert 0 <= cl8_tiles <= 152 // 8
-        print("autotune %s: tensor cores from %d ciphertexts, clusters of 8 up to %d tiles"
-              % (name, cross, cl8_tiles))
+        assert 0 <= cl16_tiles <= 152 // 16
+        print("autotune %s: tensor cores from %d ciphertexts, clusters of 8 up to %d tiles, "
+              "of 16 up to %d tiles" % (name, cross, cl8_tiles, cl16_tiles))
     luts = _luts(P, 2)
     lut = fhe.lut_create(K, luts)
     for count in (100, 1500):
