@@ -239,18 +239,21 @@ int fhe_tc_plan_query(const fhe_params *params, fhe_tc_plan *out);
 
 /* What FHE_VARIANT_AUTO and the tensor-core path currently use: the batch
  * size from which AUTO picks tensor cores (UINT64_MAX: never) and the most
- * 256-ciphertext tiles a batch may have to run on clusters of 8 and of 16
- * (the device limit before fhe_pbs_autotune; 0: never; -1: the device
- * limit, not yet queried).  tc_cl16_tiles may be NULL.  Host only.
- * Errors: FHE_EINVAL. */
+ * 256-ciphertext tiles a batch may have to run on clusters of 8, of 16, and
+ * spread over two clusters of 16 (the device limit before fhe_pbs_autotune;
+ * 0: never, e.g. the device refused a cooperative clustered launch; -1: the
+ * device limit, not yet queried).  tc_cl16_tiles and tc_split_tiles may be
+ * NULL.  Host only.  Errors: FHE_EINVAL. */
 int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles,
-                   int32_t *tc_cl16_tiles);
+                   int32_t *tc_cl16_tiles, int32_t *tc_split_tiles);
 
 /* Options of the tensor-core path, for measurements and tuning (no
  * counterpart in the paper); results are bit-identical under every option.
  *   FHE_TC_OPT_CLUSTER: 4, 8 or 16 CTAs per 256-ciphertext tile for every
  *     batch that fits in one wave of that shape (others use clusters of 4),
- *     or 0 for the tuned rule (16 up to the 16-CTA limit, then 8, then 4).
+ *     32 for each tile spread over two clusters of 16 (a cooperative launch;
+ *     batches of up to half the 16-CTA clusters, else clusters of 16), or 0
+ *     for the tuned rule (32 up to its limit, then 16, 8, 4).
  *   FHE_TC_OPT_MULTICAST (clusters of 16 only): 1 = digit tiles copied to
  *     all CTAs that hold the same rows by cluster-multicast copies, 0 = each
  *     CTA copies whole tiles, -1 = the build's default (multicast in the

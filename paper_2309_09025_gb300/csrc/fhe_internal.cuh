@@ -143,6 +143,12 @@ struct fhe_keys {
   int tc_force_mc;
   // L2 evict-last policy on the digit operand (1), none (0), default (-1)
   int tc_l2_hints;
+  // tiles spread over two 16-CTA clusters: cooperative clustered launches
+  // work on this device (1), were refused (0), not tried yet (-1); and the
+  // most tiles run that way (-1: up to half the 16-CTA clusters)
+  int tc_split_ok;
+  int tc_split_tiles;
+  uint32_t *d_tsync;     // per-tile barrier counters of the split shape
   // tensor-core key layout (built on first use of FHE_VARIANT_TC)
   void *d_bsk_tc;
   size_t bsk_tc_bytes;

@@ -165,6 +165,7 @@ static void keys_release(fhe_keys *K) {
   cudaFree(K->d_bsk_tc);
   cudaFree(K->d_acc_tc);
   cudaFree(K->d_digits_tc);
+  cudaFree(K->d_tsync);
   cudaFree(K->d_fft_twist);
   cudaFree(K->d_fft_tw);
   cudaFree(K->d_fft_kspec);
@@ -196,6 +197,8 @@ extern "C" int fhe_keygen_from_seed(const fhe_params *prm, uint64_t seed, size_t
   K->tc_cl16_tiles = -1;
   K->tc_force_mc = -1;
   K->tc_l2_hints = -1;
+  K->tc_split_ok = -1;
+  K->tc_split_tiles = -1;
   const uint64_t bsk_words = (uint64_t)P.n * P.ggsw_words();
   const uint64_t ksk_words = (uint64_t)P.k * P.N * P.l_ks * (P.n + 1u);
   bool ok = cudaMalloc(&K->d_lwe_key, sizeof(uint32_t) * P.n) == cudaSuccess &&

@@ -251,6 +251,35 @@ __device__ __forceinline__ void tc2_commit_ctas(uint64_t *bar, uint16_t mask) {
   tc2_commit_each(bar, mask);
 }
 #endif
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Barrier over the GC clusters that share one tile: the cluster barrier, then
+// one thread per cluster publishes its cluster's writes at GPU scope on the
+// tile's counter and waits (bounded, two seconds) until every cluster of the
+// tile has arrived k times, then the cluster barrier again.  An aborted
+// cluster keeps arriving, so its partners never wait for it.  The launch is
+// cooperative, so all clusters of a tile are resident together.
+template <int GC>
+__device__ __forceinline__ void tile_sync(uint32_t *ctr, uint32_t &k, volatile int *abort) {
+  cluster_sync_all();
+  if constexpr (GC > 1) {
+    ++k;
+    if (threadIdx.x == 0 && cluster_rank() == 0) {
+      __threadfence();
+      atomicAdd(ctr, 1u);
+      const uint32_t target = (uint32_t)GC * k;
+      if (!*abort && ld_acquire_gpu(ctr) < target) {
+        const uint64_t t0 = global_ns();
+        while (ld_acquire_gpu(ctr) < target)
+          if (global_ns() - t0 > 2000000000ull) { *abort = 1; break; }
+      }
+    }
+    cluster_sync_all();
+  }
+}
 // Arrive on this CTA's barrier, releasing this thread's prior writes (and
 // those ordered before them) at CTA scope.
 __device__ __forceinline__ void mbar_arrive_local(uint64_t *bar) {
@@ -379,22 +408,31 @@ __host__ __device__ inline uint64_t tc_tile_dig_halves(uint32_t N, uint32_t RR) 
 // and step) or 16 (eight pairs, a quarter; a non-portable cluster size, for
 // batches that fit in the clusters of 16 the GPU holds at once).  MC: digit
 // tiles by cluster-multicast copies (compiled only into single-GPU builds).
-template <int N, int CL, bool MC>
+template <int N, int CL, int GC, bool MC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     k_blind_rotate_tc(Params P, const __half *__restrict__ hk,
                       const uint32_t *__restrict__ ct_in, size_t count,
                       const __grid_constant__ LutArgs lut,
                       uint32_t *__restrict__ acc_g, __half *__restrict__ dig_g,
                       uint32_t chunk_r, uint32_t sub_shift, uint32_t *__restrict__ big_out,
-                      int *status, uint32_t opts) {
+                      int *status, uint32_t opts, uint32_t *__restrict__ tsync) {
   constexpr uint32_t LOG2_2N = (N == 1024) ? 11 : 12;
   constexpr uint32_t KBLK = N / kKB;             // A tiles per digit row r
   constexpr uint32_t KH = N / kBK;               // B windows per digit row
   constexpr uint32_t KT = kBK / kKB;             // A tiles per B window
   constexpr uint32_t TILE_H = kATile / 2;        // fp16 elements of one A tile
   constexpr uint32_t NP = CL / 2;                 // CTA pairs per cluster
-  constexpr uint32_t PPJ = NP / 2;                // pairs per output polynomial
-  constexpr uint32_t RPC = kBh / NP;              // digit rows each CTA of a half makes
+  constexpr uint32_t TP = GC * NP;                // CTA pairs per tile (GC clusters)
+  constexpr uint32_t PPJ = TP / 2;                // pairs per output polynomial
+  constexpr uint32_t RPC = kBh / TP;              // digit rows each CTA of a half makes
+  constexpr uint32_t UPJ = 2u * (N / kBN);        // (block, limb pair) units per polynomial
+  constexpr uint32_t UPP = UPJ / PPJ;             // units per pair
+  constexpr uint32_t NLP = (UPP >= 2u) ? 2u : 1u;  // limb pairs per block of a pair
+  constexpr uint32_t NBLK = UPP / NLP;            // blocks of 256 coefficients per pair
+  // one limb pair per pair: the two pairs of a block add into its accumulators
+  constexpr bool RED = (NLP == 1u);
+  static_assert(UPP >= 1u && UPJ % PPJ == 0u, "tile shape");
+  static_assert(GC == 1 || !MC, "multicast copies stay within one cluster");
   constexpr uint32_t G = 4096u / N;              // ciphertexts per staged group (32 KB)
   constexpr uint32_t NGROUP = RPC / G;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -415,13 +453,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t n = P.n, l = P.l, R = 2u * l;
   const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
   const uint32_t q = cluster_rank();
-  const uint32_t pr = q / 2u;               // pair index
-  const uint32_t pj = pr / PPJ;             // output polynomial of the pair
-  const uint32_t bsub = pr % PPJ;           // which share of the blocks
+  const uint32_t pr = q / 2u;               // pair index within the cluster
+  const uint32_t gci = (uint32_t)((blockIdx.x / CL) % GC);  // cluster within the tile
+  const uint32_t gp = gci * NP + pr;        // pair index within the tile
+  const uint32_t pj = gp / PPJ;             // output polynomial of the pair
+  const uint32_t bsub = gp % PPJ;           // which share of the units
   const uint32_t hh = q % 2u;               // ciphertext half (MMA rows 128 hh ..)
   const uint32_t lead = q & ~1u;            // rank of the pair's leader (issues the MMAs)
   const bool leader = (hh == 0u);
-  const uint64_t tile = blockIdx.x / CL;
+  const uint64_t tile = blockIdx.x / (CL * GC);
   const size_t base = (size_t)tile * kBt;
   // With sub_shift > 0 every gadget digit d is split into two signed
   // sub-digits d = hi * 2^sub_shift + lo (rows r and R + r of the digit
@@ -431,9 +471,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t *acc = acc_g + tile * tc_tile_acc_words(N);           // [256][2][N]
   __half *dig = dig_g + tile * tc_tile_dig_halves(N, RR);
   __half *dig_h = dig + (uint64_t)hh * RR * KBLK * TILE_H;        // this half's digit rows
-  const uint32_t row0 = kBh * hh + RPC * pr;  // first ciphertext whose digits this CTA makes
-  const uint32_t nblk = N / kBN / PPJ;        // blocks of 256 output coefficients of this pair
-  const uint32_t blk0 = bsub * nblk;
+  const uint32_t row0 = kBh * hh + RPC * gp;  // first ciphertext whose digits this CTA makes
+  // this pair's units: blocks blk0 .. + NBLK, limb pairs lp0 .. + NLP of each
+  const uint32_t nblk = NBLK;
+  const uint32_t blk0 = bsub * UPP / 2u;
+  const uint32_t lp0 = (NLP == 1u) ? (bsub * UPP) % 2u : 0u;
+  uint32_t *tile_ctr = (GC > 1) ? tsync + tile : nullptr;
+  uint32_t tile_k = 0;  // tile barriers passed
   const uint32_t nchunk = RR / chunk_r;
   const uint64_t strip_halves = 2ull * N;  // compact key entries per strip
   const uint16_t pair_mask = (uint16_t)(3u << lead);
@@ -490,7 +534,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  cluster_sync_all();
+  tile_sync<GC>(tile_ctr, tile_k, &s_abort);
 
   const uint32_t total_bits = l * P.log2_bg;
   const uint32_t Bmask = (1u << P.log2_bg) - 1u, Bhalf = 1u << (P.log2_bg - 1u);
@@ -511,6 +555,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     }
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // accumulator rows other CTAs (other clusters too) updated
+      asm volatile("fence.proxy.async.global;" ::: "memory");
       for (uint32_t g = 0; g < kGBuf && g < NGROUP; ++g) {
         const uint32_t bf = (g_it + g) % kGBuf;
         mbar_expect_tx(&g_full[bf], 32768u);
@@ -532,7 +578,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       for (uint32_t item = warp; got && item < ITEMS; item += kThreads / 32u) {
         const uint32_t cb = item % NB, j = (item / NB) & 1u, gi = item / (2u * NB);
         const uint32_t bl = g * G + gi;             // 0..RPC-1
-        const uint32_t bm = RPC * pr + bl;          // MMA row within this half
+        const uint32_t bm = RPC * gp + bl;          // MMA row within this half
         const uint32_t a = s_abar[bl];
         const uint32_t *Pj = sacc + (gi * 2u + j) * N;
         uint32_t xr[2][4];
@@ -634,7 +680,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     // bulk copies.  The barrier is cluster-wide because the partner CTA
     // multicasts into this CTA's A stages, which staged accumulators until now.
     asm volatile("fence.proxy.async;" ::: "memory");
-    cluster_sync_all();
+    tile_sync<GC>(tile_ctr, tile_k, &s_abort);
 
     // ---- external product units (block, chunk, limb pair) of output
     // polynomial pj: each A tile feeds both limbs of the pair (accumulators
@@ -649,7 +695,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         if (!MC) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
-            for (uint32_t lp = 0; lp < 2u; ++lp)
+            for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t r = ch * chunk_r + rr;
@@ -682,7 +728,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
         const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
         for (uint32_t ch = 0; ch < nchunk; ++ch)
-          for (uint32_t lp = 0; lp < 2u; ++lp)
+          for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp)
             for (uint32_t rr = 0; rr < chunk_r; ++rr)
               for (uint32_t kh = 0; kh < KH; ++kh) {
                 const uint32_t r = ch * chunk_r + rr;
@@ -740,7 +786,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       if (lane == 0 && leader) {
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
-            for (uint32_t lp = 0; lp < 2u; ++lp) {
+            for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
               if (u_it >= 1u) wait_bounded(t_empty, (u_it - 1u) & 1u, &s_abort);
               tc_fence_after();
               uint32_t accum = 0;
@@ -784,7 +830,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         // (its B windows are announced by its key-window warp)
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
-            for (uint32_t lp = 0; lp < 2u; ++lp)
+            for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp)
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   for (uint32_t kb = 0; kb < KT; ++kb) {
@@ -805,14 +851,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
         uint32_t *dst = acc + ((uint64_t)row * 2u + pj) * N + blk * kBN + half * 128u;
         uint32_t outv[128];
-        // ACC of this block, loaded while the block's MMAs run
+        if (RED) {
+          // the other limb pair of this block is another pair's: both add
 #pragma unroll
-        for (int k = 0; k < 128; k += 4) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(dst + k);
-          outv[k] = v.x; outv[k + 1] = v.y; outv[k + 2] = v.z; outv[k + 3] = v.w;
+          for (int k = 0; k < 128; ++k) outv[k] = 0u;
+        } else {
+          // ACC of this block, loaded while the block's MMAs run
+#pragma unroll
+          for (int k = 0; k < 128; k += 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(dst + k);
+            outv[k] = v.x; outv[k + 1] = v.y; outv[k + 2] = v.z; outv[k + 3] = v.w;
+          }
         }
         for (uint32_t ch = 0; ch < nchunk; ++ch)
-          for (uint32_t lp = 0; lp < 2u; ++lp) {
+          for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
             const uint32_t sub = (ch * chunk_r >= R) ? sub_shift : 0u;
             const bool got = wait_bounded(t_full, u_it & 1u, &s_abort);
             const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
@@ -844,15 +896,22 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
             ++u_it;
           }
         if (!__any_sync(0xffffffffu, s_abort != 0)) {
+          if (RED) {
+            // additions mod 2^32 commute: the result does not depend on
+            // which pair adds first
 #pragma unroll
-          for (int k = 0; k < 128; k += 4)
-            *reinterpret_cast<uint4 *>(dst + k) = make_uint4(outv[k], outv[k + 1], outv[k + 2], outv[k + 3]);
+            for (int k = 0; k < 128; ++k) atomicAdd(dst + k, outv[k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 128; k += 4)
+              *reinterpret_cast<uint4 *>(dst + k) = make_uint4(outv[k], outv[k + 1], outv[k + 2], outv[k + 3]);
+          }
         }
       }
       // the next step's digit phase reads ACC through bulk copies
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
-    cluster_sync_all();
+    tile_sync<GC>(tile_ctr, tile_k, &s_abort);
   }
 
   // Every MMA of the pair has completed before TMEM is released (on the
@@ -939,7 +998,7 @@ static uint32_t tc_digit_rows(const Params &P) { return tc_sub_shift(P) ? 2u * P
 
 int tc_prepare(fhe_keys *K) {
   const Params &P = K->P;
-  if (K->d_bsk_tc && K->d_acc_tc && K->d_digits_tc) return FHE_OK;
+  if (K->d_bsk_tc && K->d_acc_tc && K->d_digits_tc && K->d_tsync) return FHE_OK;
   // compact Hankel key: 2N fp16 per (key row, polynomial, limb)
   const uint64_t strips = (uint64_t)P.n * P.rows() * 2u * 4u;
   K->bsk_tc_bytes = strips * 2u * P.N * sizeof(__half);
@@ -950,6 +1009,7 @@ int tc_prepare(fhe_keys *K) {
   if (cudaMalloc(&K->d_digits_tc, sizeof(__half) * tiles * tc_tile_dig_halves(P.N, tc_digit_rows(P))) !=
       cudaSuccess)
     return FHE_ENOMEM;
+  if (cudaMalloc(&K->d_tsync, sizeof(uint32_t) * tiles) != cudaSuccess) return FHE_ENOMEM;
   k_hankel_compact<<<152u * 16u, 256>>>(P, K->d_bsk, (__half *)K->d_bsk_tc);
   note_launches(1);
   FHE_CUDA_TRY(cudaGetLastError());
@@ -967,23 +1027,26 @@ int pbs_prepare(fhe_keys *K, int variant) {
   return tc_prepare(K);
 }
 
-using TcKernel = decltype(&k_blind_rotate_tc<1024, 4, false>);
+using TcKernel = decltype(&k_blind_rotate_tc<1024, 4, 1, false>);
 
 // Instance of the blind rotation for ring size N, cluster size cl (4, 8 or
-// 16 CTAs per 256-ciphertext tile) and digit-tile copy form.  The single-GPU
-// build compiles multicast instances for every cluster size and per-CTA ones
-// for clusters of 16; the replica build only per-CTA ones.
+// 16 CTAs per 256-ciphertext tile) and digit-tile copy form, or (split) the
+// tile spread over two clusters of 16.  The single-GPU build compiles
+// multicast instances for every cluster size and per-CTA ones for clusters
+// of 16; the replica build only per-CTA ones.  The split instance copies per
+// CTA in both.
 template <int N>
-static TcKernel tc_kernel(int cl, bool mc) {
+static TcKernel tc_kernel(int cl, bool mc, bool split = false) {
+  if (split) return k_blind_rotate_tc<N, 16, 2, false>;
 #ifndef FHE_NO_MULTICAST
-  if (mc) return cl == 16 ? k_blind_rotate_tc<N, 16, true>
-                          : (cl == 8 ? k_blind_rotate_tc<N, 8, true> : k_blind_rotate_tc<N, 4, true>);
-  if (cl == 16) return k_blind_rotate_tc<N, 16, false>;
+  if (mc) return cl == 16 ? k_blind_rotate_tc<N, 16, 1, true>
+                          : (cl == 8 ? k_blind_rotate_tc<N, 8, 1, true> : k_blind_rotate_tc<N, 4, 1, true>);
+  if (cl == 16) return k_blind_rotate_tc<N, 16, 1, false>;
   return nullptr;
 #else
   (void)mc;
-  return cl == 16 ? k_blind_rotate_tc<N, 16, false>
-                  : (cl == 8 ? k_blind_rotate_tc<N, 8, false> : k_blind_rotate_tc<N, 4, false>);
+  return cl == 16 ? k_blind_rotate_tc<N, 16, 1, false>
+                  : (cl == 8 ? k_blind_rotate_tc<N, 8, 1, false> : k_blind_rotate_tc<N, 4, 1, false>);
 #endif
 }
 
@@ -1012,22 +1075,29 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   if (rc) return rc;
   const uint32_t chunk_r = tc_chunk_r(P), sub_shift = tc_sub_shift(P);
   const TcSmem S = tc_smem();
-  auto pick = [&](int cl, bool mc) { return P.N == 1024u ? tc_kernel<1024>(cl, mc) : tc_kernel<2048>(cl, mc); };
+  auto pick = [&](int cl, bool mc, bool split = false) {
+    return P.N == 1024u ? tc_kernel<1024>(cl, mc, split) : tc_kernel<2048>(cl, mc, split);
+  };
   // clusters of 4 and 8 copy digit tiles as the build does; clusters of 16
   // may be switched to per-CTA copies (fhe_pbs_set_tc_shape)
   const bool mc16 = (K->tc_force_mc < 0 || !kTcMulticast) ? kTcMulticast : (K->tc_force_mc != 0);
   TcKernel k4 = pick(4, kTcMulticast), k8 = pick(8, kTcMulticast), k16 = pick(16, mc16);
-  for (TcKernel k : {k4, k8, k16})
+  TcKernel k32 = pick(16, false, true);
+  for (TcKernel k : {k4, k8, k16, k32})
     FHE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   // 16 CTAs per cluster is a non-portable size (where refused, the occupancy
   // query below reports no such clusters and the shape is never used)
-  if (cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-    (void)cudaGetLastError();
-    K->tc_cl16_max = 0;
-  }
+  for (TcKernel k : {k16, k32})
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      K->tc_cl16_max = 0;
+    }
   // clusters of 8 and 16 the device holds at once (once per key handle)
   if (K->tc_cl8_max < 0) K->tc_cl8_max = tc_max_clusters(k8, 8, S.total);
   if (K->tc_cl16_max < 0) K->tc_cl16_max = tc_max_clusters(k16, 16, S.total);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FHE_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  const bool capturing = (cap != cudaStreamCaptureStatusNone);
   for (size_t s0 = 0; s0 < count; s0 += K->ws_cap) {
     const size_t cnt = (count - s0 < K->ws_cap) ? count - s0 : K->ws_cap;
     const LutArgs la = lut_args(lut, seg_end, s0);
@@ -1041,22 +1111,61 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
                                                                                  : K->tc_cl16_max;
     const int lim8 = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
                                                                             : K->tc_cl8_max;
+    // Batches of up to half the 16-CTA clusters may spread each tile over
+    // two of them (32 CTAs per tile, half the work per CTA and step again),
+    // a cooperative launch: tried eagerly first, and used inside a stream
+    // capture only once an eager launch has succeeded (a refused launch
+    // would invalidate the capture).
+    const int split_max = (K->tc_split_ok > 0 || (K->tc_split_ok < 0 && !capturing)) ? K->tc_cl16_max / 2 : 0;
+    const int lim32 = (K->tc_split_tiles >= 0 && K->tc_split_tiles < split_max) ? K->tc_split_tiles
+                                                                               : split_max;
     int cl = 4;
     if (K->tc_force_cl) {
-      if (K->tc_force_cl == 16 && tiles <= K->tc_cl16_max) cl = 16;
-      else if (K->tc_force_cl == 8 && tiles <= K->tc_cl8_max) cl = 8;
+      if (K->tc_force_cl == 32 && tiles <= split_max) cl = 32;
+      else if (K->tc_force_cl >= 16 && tiles <= K->tc_cl16_max) cl = 16;
+      else if (K->tc_force_cl >= 8 && tiles <= K->tc_cl8_max) cl = 8;
+    } else if (tiles <= lim32) {
+      cl = 32;
     } else if (tiles <= lim16) {
       cl = 16;
     } else if (tiles <= lim8) {
       cl = 8;
     }
-    TcKernel kern = (cl == 16) ? k16 : (cl == 8 ? k8 : k4);
     const bool prof = (s0 == 0) && K->prof_ev0;
     if (prof) { FHE_CUDA_TRY(record_prof_event(K->prof_ev0, st)); K->prof_count = cnt; }
-    kern<<<(unsigned)tiles * (unsigned)cl, kThreads, S.total, st>>>(
-        P, (const __half *)K->d_bsk_tc, ct_in + s0 * (P.n + 1u), cnt, la, K->d_acc_tc,
-        (__half *)K->d_digits_tc, chunk_r, sub_shift, K->d_big, K->d_status,
-        K->tc_l2_hints > 0 ? 1u : 0u);
+    const __half *hk = (const __half *)K->d_bsk_tc;
+    const uint32_t *in = ct_in + s0 * (P.n + 1u);
+    __half *dig = (__half *)K->d_digits_tc;
+    const uint32_t opts = K->tc_l2_hints > 0 ? 1u : 0u;
+    bool launched = false;
+    if (cl == 32) {
+      // cooperative: the two clusters of a tile wait on each other
+      FHE_CUDA_TRY(cudaMemsetAsync(K->d_tsync, 0, sizeof(uint32_t) * (size_t)tiles, st));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)tiles * 32u);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = S.total;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, k32, P, hk, in, cnt, la, K->d_acc_tc, dig, chunk_r, sub_shift, K->d_big,
+                             K->d_status, opts, K->d_tsync) == cudaSuccess) {
+        launched = true;
+        if (!capturing) K->tc_split_ok = 1;
+      } else {  // the device refuses a cooperative clustered launch: never again
+        (void)cudaGetLastError();
+        K->tc_split_ok = 0;
+        cl = 16;
+      }
+    }
+    if (!launched) {
+      TcKernel kern = (cl == 16) ? k16 : (cl == 8 ? k8 : k4);
+      kern<<<(unsigned)tiles * (unsigned)cl, kThreads, S.total, st>>>(
+          P, hk, in, cnt, la, K->d_acc_tc, dig, chunk_r, sub_shift, K->d_big, K->d_status, opts, nullptr);
+    }
     note_launches(1);
     FHE_CUDA_TRY(cudaGetLastError());
     if (prof) FHE_CUDA_TRY(record_prof_event(K->prof_ev1, st));
@@ -1163,6 +1272,9 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
   if (ok && rc == FHE_OK && K->tc_cl8_max > 0 && cmax >= 256u) cl8_tiles = tune_shape(4, 8, K->tc_cl8_max);
   if (ok && rc == FHE_OK && K->tc_cl16_max > 0 && cmax >= 256u)
     cl16_tiles = tune_shape(K->tc_cl8_max > 0 ? 8 : 4, 16, K->tc_cl16_max);
+  int split_tiles = -1;
+  if (ok && rc == FHE_OK && K->tc_split_ok != 0 && K->tc_cl16_max >= 2 && cmax >= 256u)
+    split_tiles = tune_shape(16, 32, K->tc_cl16_max / 2);
   if (!ok && rc == FHE_OK) { (void)cudaGetLastError(); rc = FHE_ECUDA; }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -1172,6 +1284,7 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
   if (rc) return rc;
   K->tc_cl8_tiles = cl8_tiles;
   K->tc_cl16_tiles = cl16_tiles;
+  K->tc_split_tiles = split_tiles;
   // tensor cores never won up to cmax: use them only above it
   K->tc_min_batch = (best == SIZE_MAX) ? 2 * cmax : (best == c_first ? 1u : best);
   *tc_min_batch = K->tc_min_batch;
@@ -1179,7 +1292,7 @@ extern "C" int fhe_pbs_autotune(fhe_keys *K, uint64_t *tc_min_batch, void *strea
 }
 
 extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t *tc_cl8_tiles,
-                              int32_t *tc_cl16_tiles) {
+                              int32_t *tc_cl16_tiles, int32_t *tc_split_tiles) {
   if (!K || !tc_min_batch || !tc_cl8_tiles) return FHE_EINVAL;
   *tc_min_batch = (K->tc_min_batch == SIZE_MAX) ? UINT64_MAX : (uint64_t)K->tc_min_batch;
   *tc_cl8_tiles = (K->tc_cl8_tiles >= 0 && K->tc_cl8_tiles < K->tc_cl8_max) ? K->tc_cl8_tiles
@@ -1187,6 +1300,11 @@ extern "C" int fhe_pbs_tuning(const fhe_keys *K, uint64_t *tc_min_batch, int32_t
   if (tc_cl16_tiles)
     *tc_cl16_tiles = (K->tc_cl16_tiles >= 0 && K->tc_cl16_tiles < K->tc_cl16_max) ? K->tc_cl16_tiles
                                                                                  : K->tc_cl16_max;
+  if (tc_split_tiles) {
+    const int smax = (K->tc_split_ok == 0 || K->tc_cl16_max < 0) ? 0 : K->tc_cl16_max / 2;
+    *tc_split_tiles = (K->tc_split_ok < 0 && K->tc_cl16_max < 0) ? -1
+                      : ((K->tc_split_tiles >= 0 && K->tc_split_tiles < smax) ? K->tc_split_tiles : smax);
+  }
   return FHE_OK;
 }
 
@@ -1194,7 +1312,7 @@ extern "C" int fhe_pbs_set_tc_option(fhe_keys *K, int option, int value) {
   if (!K) return FHE_EINVAL;
   switch (option) {
     case FHE_TC_OPT_CLUSTER:
-      if (value != 0 && value != 4 && value != 8 && value != 16) return FHE_EINVAL;
+      if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32) return FHE_EINVAL;
       K->tc_force_cl = value;
       return FHE_OK;
     case FHE_TC_OPT_MULTICAST:

@@ -158,7 +158,7 @@ def lib():
             "fhe_lut_create_spaces": (ctypes.c_int, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(vp)]),
             "fhe_pbs_batch_groups": (ctypes.c_int, [vp, vp, sz, vp, vp, vp, ctypes.c_int, vp]),
             "fhe_pbs_tuning": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(i32),
-                                              ctypes.POINTER(i32)]),
+                                              ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fhe_pbs_set_tc_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
             "fhe_tc_plan_query": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(TcPlan)]),
             "fhe_snn_stream_stage": (ctypes.c_int, [vp, vp, sz, vp, ctypes.c_int, vp]),
@@ -261,11 +261,12 @@ class Keys:
 
     def tuning(self):
         """fhe_pbs_tuning: (smallest batch AUTO runs on tensor cores or None,
-        most tiles run on clusters of 8, most tiles run on clusters of 16)."""
-        v, c, c16 = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int32()
+        most tiles run on clusters of 8, of 16, spread over two clusters of 16)."""
+        v, c, c16, c32 = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib().fhe_pbs_tuning(self.handle, ctypes.byref(v), ctypes.byref(c),
-                                    ctypes.byref(c16)), "pbs_tuning")
-        return (None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value), int(c16.value)
+                                    ctypes.byref(c16), ctypes.byref(c32)), "pbs_tuning")
+        return ((None if v.value == (1 << 64) - 1 else int(v.value)), int(c.value), int(c16.value),
+                int(c32.value))
 
     def set_tc_option(self, option, value):
         """fhe_pbs_set_tc_option: TC_OPT_CLUSTER (0, 4, 8, 16),

@@ -264,7 +264,8 @@ def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
 @pytest.mark.parametrize("name,count", [("P630", 389), ("P750", 613)])
 def test_tc_every_tile_shape_bit_exact(fhe, oracle_keys, name, count):
     """Every shape of the tensor-core kernel forced in turn (fhe_pbs_set_tc_option):
-    256-ciphertext tiles on clusters of 4, 8 and 16 CTAs, the 16-CTA shape
+    256-ciphertext tiles on clusters of 4, 8 and 16 CTAs and spread over two
+    clusters of 16 (the two pairs of each block adding into it), the 16-CTA shape
     with multicast and with per-CTA digit-tile copies, with and without the
     L2 policy on the digit operand; all outputs of both
     LIF tables bit-identical to the CUDA-core path, tile-edge outputs to the
@@ -281,13 +282,15 @@ def test_tc_every_tile_shape_bit_exact(fhe, oracle_keys, name, count):
     ref = O.pbs(P, OK, u32(ct)[idx], luts, nthreads=NTHREADS)
     assert np.array_equal(ref_gpu[:, idx], ref)
     try:
-        for cluster, mc, hint in [(4, -1, 0), (8, -1, 0), (16, 1, 0), (16, 0, 0), (4, -1, 1),
-                                  (16, 1, 1)]:
+        for cluster, mc, hint in [(4, -1, 0), (8, -1, 0), (16, 1, 0), (16, 0, 0), (32, -1, 0),
+                                  (4, -1, 1), (16, 1, 1)]:
             K.set_tc_option(fhe.TC_OPT_CLUSTER, cluster)
             K.set_tc_option(fhe.TC_OPT_MULTICAST, mc)
             K.set_tc_option(fhe.TC_OPT_L2_HINTS, hint)
             got = u32(pbs(fhe, K, ct, lut, "TC"))
             assert np.array_equal(got, ref_gpu), f"clusters of {cluster}, multicast {mc}, L2 {hint}"
+            if cluster == 32:  # the split shape really ran (not a fallback to 16)
+                assert K.tuning()[3] >= -(-count // 256), "two-cluster tiles were not launched"
     finally:
         for opt, v in ((fhe.TC_OPT_CLUSTER, 0), (fhe.TC_OPT_MULTICAST, -1), (fhe.TC_OPT_L2_HINTS, -1)):
             K.set_tc_option(opt, v)
@@ -431,7 +434,7 @@ def test_autotuned_variant_is_bit_exact(fhe, oracle_keys, name):
     P, K = gpu_keys(fhe, name, 3)
     p = 1 << P["log2_p"]
     cross = K.autotune()
-    tuned, cl8_tiles, cl16_tiles = K.tuning()
+    tuned, cl8_tiles, cl16_tiles, split_tiles = K.tuning()
     assert tuned == cross
     if name == "P64":
         assert cross is None
@@ -439,8 +442,10 @@ def test_autotuned_variant_is_bit_exact(fhe, oracle_keys, name):
         assert cross is not None and 1 <= cross <= 8192
         assert 0 <= cl8_tiles <= 152 // 8
         assert 0 <= cl16_tiles <= 152 // 16
+        assert 0 <= split_tiles <= 152 // 32
         print("autotune %s: tensor cores from %d ciphertexts, clusters of 8 up to %d tiles, "
-              "of 16 up to %d tiles" % (name, cross, cl8_tiles, cl16_tiles))
+              "of 16 up to %d tiles, two clusters of 16 per tile up to %d tiles"
+              % (name, cross, cl8_tiles, cl16_tiles, split_tiles))
     luts = _luts(P, 2)
     lut = fhe.lut_create(K, luts)
     for count in (100, 1500):
