@@ -390,7 +390,7 @@ __host__ __device__ inline TcSmem tc_smem() {
   s.a = o; o += kAStages * kATile;
   s.b = o; o += 2u * 2u * kBWin;
   s.h = o; o += 2u * 2u * kHStage;
-  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 + 2 mbarriers
+  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 + 2 + 1 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
@@ -446,6 +446,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t *t_full = b_full + 6, *t_empty = b_full + 7, *done = b_full + 8;
   uint64_t *g_full = b_full + 9;  // staging buffers of the digit phase
   uint64_t *h_full = g_full + kGBuf;  // compact key entries of each B stage
+  // t_empty: the epilogue has drained limb 0's accumulator (TMEM columns
+  // 0..255) of the unit; t_empty1: limb 1's (256..511)
+  uint64_t *t_empty1 = h_full + 2;
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
   __shared__ uint32_t s_abar[RPC];  // a~_i of the ciphertexts whose digits this CTA makes
@@ -501,7 +504,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     }
     for (uint32_t s = 0; s < kGBuf; ++s) mbar_init(&g_full[s], 1);
     for (int s = 0; s < 2; ++s) mbar_init(&h_full[s], 1);
-    mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(done, 1);
+    mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(t_empty1, 16); mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -784,12 +787,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       __syncwarp();
     } else if (warp == 1) {
       if (lane == 0 && leader) {
+        // Limb 0's accumulator is released by the epilogue before limb 1's:
+        // a unit starts with limb 0's MMAs as soon as it is free, and the
+        // limb-1 MMAs of its first key window's tiles wait (their A stages
+        // held) until limb 1's accumulator is drained too, so limb 1's drain
+        // overlaps limb 0's MMAs.  Within a limb every partial sum is an
+        // exact fp32 integer, so the order of the additions does not matter.
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
             for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
               if (u_it >= 1u) wait_bounded(t_empty, (u_it - 1u) & 1u, &s_abort);
               tc_fence_after();
-              uint32_t accum = 0;
+              bool z1_free = (u_it == 0u);
+              uint32_t acc0 = 0, acc1 = 0;
+              uint32_t def_as[KT], def_kb[KT], ndef = 0;  // tiles whose limb-1 MMAs wait
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t bs = b_it & 1u;
@@ -797,27 +808,56 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                   wait_bounded_cluster(&b_peer[bs], (b_it >> 1) & 1u, &s_abort);
                   tc_fence_after();
                   const uint32_t bbase = smem_u32(sB + bs * 2u * kBWin);
+                  // limb z's MMAs of the tile in stage `as` (K position kb of the window)
+                  auto mma_tile = [&](uint32_t as, uint32_t kb, uint32_t z, uint32_t &accz) {
+                    const uint32_t abase = smem_u32(sA + as * kATile);
+#pragma unroll
+                    for (uint32_t s = 0; s < kKB / 16u; ++s) {
+                      const uint64_t ad = smem_desc(abase + s * 256u, 128u, kASBO);
+                      const uint64_t bd = smem_desc(bbase + z * kBWin + ((kKB / 8u) * kb + 2u * s) * 128u,
+                                                    128u, 128u);
+                      tc2_mma_f16(tmem + z * (uint32_t)kBN, ad, bd, idesc, accz);
+                      accz = 1u;
+                    }
+                  };
+                  auto flush = [&]() {
+                    for (uint32_t d = 0; d < ndef; ++d) {
+                      mma_tile(def_as[d], def_kb[d], 1u, acc1);
+                      tc2_commit_ctas(&a_empty[def_as[d]], all_mask);
+                    }
+                    ndef = 0;
+                  };
                   for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
                     wait_bounded(&a_peer[as], (a_it / kAStages) & 1u, &s_abort);
                     tc_fence_after();
                     if (!s_abort) {
-                      const uint32_t abase = smem_u32(sA + as * kATile);
-#pragma unroll
-                      for (uint32_t s = 0; s < kKB / 16u; ++s) {
-                        const uint64_t ad = smem_desc(abase + s * 256u, 128u, kASBO);
-#pragma unroll
-                        for (uint32_t z = 0; z < 2u; ++z) {
-                          const uint64_t bd = smem_desc(bbase + z * kBWin + ((kKB / 8u) * kb + 2u * s) * 128u,
-                                                        128u, 128u);
-                          tc2_mma_f16(tmem + z * (uint32_t)kBN, ad, bd, idesc, accum);
-                        }
-                        accum = 1u;
+                      mma_tile(as, kb, 0u, acc0);
+                      if (!z1_free && mbar_try_wait(t_empty1, (u_it - 1u) & 1u)) {
+                        tc_fence_after();
+                        z1_free = true;
                       }
-                      tc2_commit_ctas(&a_empty[as], all_mask);
+                      if (z1_free) {
+                        flush();
+                        mma_tile(as, kb, 1u, acc1);
+                        tc2_commit_ctas(&a_empty[as], all_mask);
+                      } else {
+                        def_as[ndef] = as;
+                        def_kb[ndef] = kb;
+                        ++ndef;
+                      }
                     }
                     ++a_it;
+                  }
+                  // the window's B stage is released only after every MMA
+                  // that reads it, deferred ones included
+                  if (ndef && !s_abort) {
+                    if (wait_bounded(t_empty1, (u_it - 1u) & 1u, &s_abort)) {
+                      tc_fence_after();
+                      z1_free = true;
+                      flush();
+                    }
                   }
                   if (!s_abort) tc2_commit_ctas(&b_empty[bs], pair_mask);
                   ++b_it;
@@ -847,7 +887,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       // columns 128 ((w - 2) / 4) .. +128 of both 256-column accumulators
       const uint32_t quarter = warp % 4u, half = (warp - 2u) / 4u;
       const uint32_t row = kBh * hh + 32u * quarter + lane;  // ciphertext row of the tile
-      const uint32_t te = cluster_addr(t_empty, lead);
+      const uint32_t te = cluster_addr(t_empty, lead), te1 = cluster_addr(t_empty1, lead);
       for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
         uint32_t *dst = acc + ((uint64_t)row * 2u + pj) * N + blk * kBN + half * 128u;
         uint32_t outv[128];
@@ -869,9 +909,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
             const bool got = wait_bounded(t_full, u_it & 1u, &s_abort);
             const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
             tc_fence_after();
-            if (ok) {
 #pragma unroll 1
-              for (uint32_t z = 0; z < 2u; ++z) {
+            for (uint32_t z = 0; z < 2u; ++z) {
+              if (ok) {
                 const uint32_t shift = 8u * (2u * lp + z) + sub;
                 const uint32_t tbase = tmem + ((32u * quarter) << 16) + z * (uint32_t)kBN + half * 128u;
                 // two 16-column buffers: the load of one overlaps the
@@ -889,10 +929,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                   if (c + 2u < 8u) tc_wait16(ra);
                 }
               }
+              // limb z's accumulator is free for the next unit's MMAs
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive_remote(z ? te1 : te);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_remote(te);
             ++u_it;
           }
         if (!__any_sync(0xffffffffu, s_abort != 0)) {
