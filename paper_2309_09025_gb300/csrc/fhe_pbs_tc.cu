@@ -390,7 +390,7 @@ __host__ __device__ inline TcSmem tc_smem() {
   s.a = o; o += kAStages * kATile;
   s.b = o; o += 2u * 2u * kBWin;
   s.h = o; o += 2u * 2u * kHStage;
-  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 + 2 + 1 mbarriers
+  s.bars = o; o += 48u * 8u;   // 3 x kAStages + 6 + 3 + 6 + 2 + 2 mbarriers
   s.tmem_slot = o; o += 16u;
   s.total = o;
   return s;
@@ -449,6 +449,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   // t_empty: the epilogue has drained limb 0's accumulator (TMEM columns
   // 0..255) of the unit; t_empty1: limb 1's (256..511)
   uint64_t *t_empty1 = h_full + 2;
+  // t_full0: the unit's limb-0 MMAs are complete (its limb-1 MMAs may still run)
+  uint64_t *t_full0 = h_full + 3;
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
   __shared__ uint32_t s_abar[RPC];  // a~_i of the ciphertexts whose digits this CTA makes
@@ -505,6 +507,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
     for (uint32_t s = 0; s < kGBuf; ++s) mbar_init(&g_full[s], 1);
     for (int s = 0; s < 2; ++s) mbar_init(&h_full[s], 1);
     mbar_init(t_full, 1); mbar_init(t_empty, 16); mbar_init(t_empty1, 16); mbar_init(done, 1);
+    mbar_init(t_full0, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -791,8 +794,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         // a unit starts with limb 0's MMAs as soon as it is free, and the
         // limb-1 MMAs of its first key window's tiles wait (their A stages
         // held) until limb 1's accumulator is drained too, so limb 1's drain
-        // overlaps limb 0's MMAs.  Within a limb every partial sum is an
-        // exact fp32 integer, so the order of the additions does not matter.
+        // overlaps limb 0's MMAs.  Symmetrically, the last key window runs
+        // all its limb-0 MMAs first and announces them (t_full0), so limb 0
+        // drains while the window's limb-1 MMAs run.  Within a limb every
+        // partial sum is an exact fp32 integer, so the order of the additions
+        // does not matter.
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
             for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
@@ -827,12 +833,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     ndef = 0;
                   };
+                  const bool last = (rr + 1u == chunk_r) && (kh + 1u == KH);
+                  uint32_t tail_as[KT], ntail = 0;  // last window: limb-1 MMAs after t_full0
                   for (uint32_t kb = 0; kb < KT; ++kb) {
                     const uint32_t as = a_it % kAStages;
                     wait_bounded(&a_full[as], (a_it / kAStages) & 1u, &s_abort);
                     wait_bounded(&a_peer[as], (a_it / kAStages) & 1u, &s_abort);
                     tc_fence_after();
-                    if (!s_abort) {
+                    if (!s_abort && last && z1_free) {
+                      mma_tile(as, kb, 0u, acc0);
+                      tail_as[ntail++] = as;
+                    } else if (!s_abort) {
                       mma_tile(as, kb, 0u, acc0);
                       if (!z1_free && mbar_try_wait(t_empty1, (u_it - 1u) & 1u)) {
                         tc_fence_after();
@@ -857,6 +868,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                       tc_fence_after();
                       z1_free = true;
                       flush();
+                    }
+                  }
+                  if (last && !s_abort) {
+                    // every limb-0 MMA of the unit is issued: announce them,
+                    // then the last window's limb-1 MMAs
+                    tc2_commit_ctas(t_full0, pair_mask);
+                    for (uint32_t d = 0; d < ntail; ++d) {
+                      mma_tile(tail_as[d], d, 1u, acc1);
+                      tc2_commit_ctas(&a_empty[tail_as[d]], all_mask);
                     }
                   }
                   if (!s_abort) tc2_commit_ctas(&b_empty[bs], pair_mask);
@@ -906,11 +926,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         for (uint32_t ch = 0; ch < nchunk; ++ch)
           for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
             const uint32_t sub = (ch * chunk_r >= R) ? sub_shift : 0u;
-            const bool got = wait_bounded(t_full, u_it & 1u, &s_abort);
-            const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
-            tc_fence_after();
 #pragma unroll 1
             for (uint32_t z = 0; z < 2u; ++z) {
+              // limb 0 is complete at t_full0, limb 1 at t_full
+              const bool got = wait_bounded(z ? t_full : t_full0, u_it & 1u, &s_abort);
+              const bool ok = __all_sync(0xffffffffu, got);  // warp-uniform for tcgen05.ld
+              tc_fence_after();
               if (ok) {
                 const uint32_t shift = 8u * (2u * lp + z) + sub;
                 const uint32_t tbase = tmem + ((32u * quarter) << 16) + z * (uint32_t)kBN + half * 128u;
