@@ -326,6 +326,8 @@ def run_ours(args):
     # workspace: one bootstrap launch holds every layer's neurons of a batch
     keys = fhe.keygen_from_seed(P, seed=3 + rank, max_batch=max(16384, -(-B * 1290 // 256) * 256))
     keys.set_tc_option(fhe.TC_OPT_L2_HINTS, args.tc_l2_hints)
+    if world == 1:
+        keys.set_tc_option(fhe.TC_OPT_MULTICAST, args.tc_multicast)
     images = synth.stroke_images(5 + rank, B)
     ct = fhe.encrypt(keys, images.reshape(-1), seed=11 + rank).view(B, 28 * 28, P["n"] + 1)
     variant = fhe.VARIANT_TC if args.variant == "tc" else fhe.VARIANT_EXACT
@@ -420,7 +422,7 @@ def run_ours(args):
                                "one batch per step: layer-skewed, one bootstrap launch per "
                                "iteration, CUDA graph per iteration",
                    "l2": "256 MiB buffer written before every timed step",
-                   "tc_l2_hints": args.tc_l2_hints,
+                   "tc_l2_hints": args.tc_l2_hints, "tc_multicast": args.tc_multicast,
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
         "ms_per_prediction": total_ms / args.steps / B,
         "pbs_per_image": per_image,
@@ -457,6 +459,9 @@ def main():
     ap.add_argument("--tc-l2-hints", type=int, default=-1,
                     help="tensor-core option: L2 evict-last policy on the digit operand "
                          "(1 on, 0 off, -1 library default)")
+    ap.add_argument("--tc-multicast", type=int, default=-1,
+                    help="tensor-core option: digit tiles by multicast (1) or per-CTA (0) copies "
+                         "(-1 library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

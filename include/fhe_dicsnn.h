@@ -254,11 +254,12 @@ int fhe_pbs_tuning(const fhe_keys *keys, uint64_t *tc_min_batch, int32_t *tc_cl8
  *     32 for each tile spread over two clusters of 16 (a cooperative launch;
  *     batches of up to half the 16-CTA clusters, else clusters of 16), or 0
  *     for the tuned rule (32 up to its limit, then 16, 8, 4).
- *   FHE_TC_OPT_MULTICAST (clusters of 16 only): 1 = digit tiles copied to
- *     all CTAs that hold the same rows by cluster-multicast copies, 0 = each
- *     CTA copies whole tiles, -1 = the build's default (multicast in the
+ *   FHE_TC_OPT_MULTICAST: 1 = digit tiles copied to all CTAs that hold the
+ *     same rows by cluster-multicast copies (each stage refilled once every
+ *     pair of the cluster is done with it), 0 = each CTA copies whole tiles
+ *     (the pairs run decoupled), -1 = the build's default (multicast in the
  *     single-GPU library; the replica library has no multicast and returns
- *     FHE_EUNSUPPORTED for 1).
+ *     FHE_EUNSUPPORTED for 1).  The split shape always copies per CTA.
  *   FHE_TC_OPT_L2_HINTS: 1 = the digit operand is stored and copied with an
  *     L2 evict-last cache policy, 0 = no policy, -1 = the default (none).
  * Host only; applies from the next call.  Errors: FHE_EINVAL (unknown

@@ -193,6 +193,10 @@ __device__ __forceinline__ void st_u2(void *p, uint2 v, bool hint, uint64_t pol)
   else
     *reinterpret_cast<uint2 *>(p) = v;
 }
+// Bring `bytes` of global memory into L2 (a hint: no data is returned).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -490,6 +494,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   uint16_t a_mask = 0;
   for (uint32_t k = 0; k < NP; ++k) a_mask |= (uint16_t)(1u << (2u * k + hh));
   const uint16_t all_mask = (uint16_t)((1u << CL) - 1u);
+  // A stage release: with multicast copies a stage of every CTA holding the
+  // same rows is refilled by all of them, so every pair's MMAs must be done
+  // with it; with per-CTA copies only this pair's (the pairs run decoupled)
+  const uint16_t ae_mask = MC ? all_mask : pair_mask;
   // opts bit 0: the digit operand is written and copied with an L2
   // evict-last policy (it is read 2 nblk times per step; the accumulators,
   // read once and written once per step, are the lines that leave L2)
@@ -499,7 +507,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     s_abort = 0;
     for (uint32_t s = 0; s < kAStages; ++s) {
-      mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], NP); mbar_init(&a_peer[s], 1);
+      mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], MC ? NP : 1u); mbar_init(&a_peer[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); mbar_init(&b_peer[s], 1);
@@ -701,7 +709,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         if (!MC) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
-            for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp)
+            for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
+              // The digit tiles depend on the digit row and K only, so every
+              // block pass re-reads the same tiles.  While a chunk is used,
+              // bring the next chunk's tiles (this CTA's share of each) into
+              // L2, so that the next pass finds them there.
+              if (lp == lp0 && !s_abort) {
+                const uint32_t nch = (ch + 1u) % nchunk;
+                const uint32_t share = MC ? (uint32_t)kATile / NP : (uint32_t)kATile;
+                for (uint32_t t = 0; t < chunk_r * KBLK; ++t) {
+                  const __half *tsrc = dig_h + (uint64_t)(nch * chunk_r * KBLK + t) * TILE_H +
+                                       (MC ? pr * (share / 2u) : 0u);
+                  prefetch_l2(tsrc, share);
+                }
+              }
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t r = ch * chunk_r + rr;
@@ -718,6 +739,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                     ++a_it;
                   }
                 }
+            }
       }
       __syncwarp();
     } else if (warp == kBWarp) {
@@ -829,7 +851,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                   auto flush = [&]() {
                     for (uint32_t d = 0; d < ndef; ++d) {
                       mma_tile(def_as[d], def_kb[d], 1u, acc1);
-                      tc2_commit_ctas(&a_empty[def_as[d]], all_mask);
+                      tc2_commit_ctas(&a_empty[def_as[d]], ae_mask);
                     }
                     ndef = 0;
                   };
@@ -852,7 +874,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                       if (z1_free) {
                         flush();
                         mma_tile(as, kb, 1u, acc1);
-                        tc2_commit_ctas(&a_empty[as], all_mask);
+                        tc2_commit_ctas(&a_empty[as], ae_mask);
                       } else {
                         def_as[ndef] = as;
                         def_kb[ndef] = kb;
@@ -876,7 +898,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                     tc2_commit_ctas(t_full0, pair_mask);
                     for (uint32_t d = 0; d < ntail; ++d) {
                       mma_tile(tail_as[d], d, 1u, acc1);
-                      tc2_commit_ctas(&a_empty[tail_as[d]], all_mask);
+                      tc2_commit_ctas(&a_empty[tail_as[d]], ae_mask);
                     }
                   }
                   if (!s_abort) tc2_commit_ctas(&b_empty[bs], pair_mask);
@@ -1103,13 +1125,11 @@ static TcKernel tc_kernel(int cl, bool mc, bool split = false) {
 #ifndef FHE_NO_MULTICAST
   if (mc) return cl == 16 ? k_blind_rotate_tc<N, 16, 1, true>
                           : (cl == 8 ? k_blind_rotate_tc<N, 8, 1, true> : k_blind_rotate_tc<N, 4, 1, true>);
-  if (cl == 16) return k_blind_rotate_tc<N, 16, 1, false>;
-  return nullptr;
 #else
   (void)mc;
+#endif
   return cl == 16 ? k_blind_rotate_tc<N, 16, 1, false>
                   : (cl == 8 ? k_blind_rotate_tc<N, 8, 1, false> : k_blind_rotate_tc<N, 4, 1, false>);
-#endif
 }
 
 // Clusters of `cl` CTAs of `kern` the device holds at once (0 when the
@@ -1140,10 +1160,10 @@ int pbs_tc(fhe_keys *K, const uint32_t *ct_in, size_t count, const fhe_lut *lut,
   auto pick = [&](int cl, bool mc, bool split = false) {
     return P.N == 1024u ? tc_kernel<1024>(cl, mc, split) : tc_kernel<2048>(cl, mc, split);
   };
-  // clusters of 4 and 8 copy digit tiles as the build does; clusters of 16
-  // may be switched to per-CTA copies (fhe_pbs_set_tc_shape)
-  const bool mc16 = (K->tc_force_mc < 0 || !kTcMulticast) ? kTcMulticast : (K->tc_force_mc != 0);
-  TcKernel k4 = pick(4, kTcMulticast), k8 = pick(8, kTcMulticast), k16 = pick(16, mc16);
+  // digit tiles copied as the build does (multicast where compiled in),
+  // unless the option asks for per-CTA copies (or multicast)
+  const bool mc = (K->tc_force_mc < 0 || !kTcMulticast) ? kTcMulticast : (K->tc_force_mc != 0);
+  TcKernel k4 = pick(4, mc), k8 = pick(8, mc), k16 = pick(16, mc);
   TcKernel k32 = pick(16, false, true);
   for (TcKernel k : {k4, k8, k16, k32})
     FHE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));

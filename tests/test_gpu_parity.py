@@ -265,7 +265,7 @@ def test_tc_matches_exact_full_batch(fhe, oracle_keys, name, count):
 def test_tc_every_tile_shape_bit_exact(fhe, oracle_keys, name, count):
     """Every shape of the tensor-core kernel forced in turn (fhe_pbs_set_tc_option):
     256-ciphertext tiles on clusters of 4, 8 and 16 CTAs and spread over two
-    clusters of 16 (the two pairs of each block adding into it), the 16-CTA shape
+    clusters of 16 (the two pairs of each block adding into it), each shape
     with multicast and with per-CTA digit-tile copies, with and without the
     L2 policy on the digit operand; all outputs of both
     LIF tables bit-identical to the CUDA-core path, tile-edge outputs to the
@@ -283,7 +283,7 @@ def test_tc_every_tile_shape_bit_exact(fhe, oracle_keys, name, count):
     assert np.array_equal(ref_gpu[:, idx], ref)
     try:
         for cluster, mc, hint in [(4, -1, 0), (8, -1, 0), (16, 1, 0), (16, 0, 0), (32, -1, 0),
-                                  (4, -1, 1), (16, 1, 1)]:
+                                  (4, 0, 0), (8, 0, 0), (4, -1, 1), (16, 1, 1)]:
             K.set_tc_option(fhe.TC_OPT_CLUSTER, cluster)
             K.set_tc_option(fhe.TC_OPT_MULTICAST, mc)
             K.set_tc_option(fhe.TC_OPT_L2_HINTS, hint)
