@@ -48,3 +48,24 @@ def test_two_gloo_ranks_agree_on_max_time_and_job_rate():
     slowest, rate = out[0]
     assert slowest == 2000.0
     assert rate == pytest.approx(5160 * 7 * 2 / 2.0)
+
+
+def test_traffic_record_is_used_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
+    """bench.py reports the ncu DRAM traffic of a blind-rotation launch only
+    while the kernel's source file still hashes to the value recorded with
+    the capture, and only for the launch size that was captured."""
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_SOURCE, "tc", "k.cu")
+    rec = tmp_path / "traffic.txt"
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
+    assert bench.recorded_traffic("tc", 9030.0)[0] is None  # no record
+    rec.write_text("# header\narm=tc kernel=k sha16=%s cts_per_launch=9030 bytes_per_launch=123 "
+                   "capture=x\n" % bench.source_sha16("k.cu"))
+    assert bench.recorded_traffic("tc", 9030.0)[0] == 123.0
+    assert bench.recorded_traffic("tc", 4096.0)[0] is None  # another launch size
+    src.write_text("kernel v2\n")
+    value, why = bench.recorded_traffic("tc", 9030.0)
+    assert value is None and "changed" in why
