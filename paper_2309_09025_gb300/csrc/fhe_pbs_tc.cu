@@ -193,10 +193,6 @@ __device__ __forceinline__ void st_u2(void *p, uint2 v, bool hint, uint64_t pol)
   else
     *reinterpret_cast<uint2 *>(p) = v;
 }
-// Bring `bytes` of global memory into L2 (a hint: no data is returned).
-__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -710,19 +706,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
         for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk)
           for (uint32_t ch = 0; ch < nchunk; ++ch)
             for (uint32_t lp = lp0; lp < lp0 + NLP; ++lp) {
-              // The digit tiles depend on the digit row and K only, so every
-              // block pass re-reads the same tiles.  While a chunk is used,
-              // bring the next chunk's tiles (this CTA's share of each) into
-              // L2, so that the next pass finds them there.
-              if (lp == lp0 && !s_abort) {
-                const uint32_t nch = (ch + 1u) % nchunk;
-                const uint32_t share = MC ? (uint32_t)kATile / NP : (uint32_t)kATile;
-                for (uint32_t t = 0; t < chunk_r * KBLK; ++t) {
-                  const __half *tsrc = dig_h + (uint64_t)(nch * chunk_r * KBLK + t) * TILE_H +
-                                       (MC ? pr * (share / 2u) : 0u);
-                  prefetch_l2(tsrc, share);
-                }
-              }
               for (uint32_t rr = 0; rr < chunk_r; ++rr)
                 for (uint32_t kh = 0; kh < KH; ++kh) {
                   const uint32_t r = ch * chunk_r + rr;
@@ -752,7 +735,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
       // its b_full (release, CTA scope) and the peer's on the leader's b_peer
       // (release, cluster scope).
       const uint32_t g = lane >> 3, rho = lane & 7u;
-      const bool odd = (rho & 1u) != 0u;
+      const uint32_t sh = (rho & 1u) * 16u;  // funnel-shift bits: odd rows start mid-word
       for (uint32_t blk = blk0; blk < blk0 + nblk; ++blk) {
         const uint32_t c0 = blk * kBN + hh * (kBN / 2u);  // this CTA's 128 columns of B
         for (uint32_t ch = 0; ch < nchunk; ++ch)
@@ -779,24 +762,26 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 if (go) go = __all_sync(0xffffffffu, wait_bounded(&h_full[bs], (b_it >> 1) & 1u, &s_abort));
                 if (go) {
-#pragma unroll
-                  for (uint32_t z = 0; z < 2u; ++z) {
-                    const uint32_t *hw = reinterpret_cast<const uint32_t *>(hst + z * kHStage);
-                    unsigned char *win = sB + (bs * 2u + z) * kBWin;
+                  // both limbs' windows in one pass (two independent chains)
+                  const uint32_t *hw0 = reinterpret_cast<const uint32_t *>(hst) + (rho >> 1);
+                  const uint32_t *hw1 = reinterpret_cast<const uint32_t *>(hst + kHStage) + (rho >> 1);
+                  unsigned char *win0 = sB + bs * 2u * kBWin + rho * 16u;
+                  unsigned char *win1 = win0 + kBWin;
 #pragma unroll 4
-                    for (uint32_t d0 = 0; d0 < kBCm; d0 += 4u) {
-                      const uint32_t d = d0 + g;
-                      if (d < kBCm) {
-                        // entries 8d + rho .. + 7 = halves rho .. rho + 7 of words 4d ..
-                        const uint32_t *w = hw + 4u * d + (rho >> 1);
-                        const uint32_t x0 = w[0], x1 = w[1], x2 = w[2], x3 = w[3], x4 = w[4];
-                        uint4 o;
-                        o.x = odd ? __funnelshift_r(x0, x1, 16) : x0;
-                        o.y = odd ? __funnelshift_r(x1, x2, 16) : x1;
-                        o.z = odd ? __funnelshift_r(x2, x3, 16) : x2;
-                        o.w = odd ? __funnelshift_r(x3, x4, 16) : x3;
-                        *reinterpret_cast<uint4 *>(win + d * 128u + rho * 16u) = o;
-                      }
+                  for (uint32_t d0 = 0; d0 < kBCm; d0 += 4u) {
+                    const uint32_t d = d0 + g;
+                    if (d < kBCm) {
+                      // entries 8d + rho .. + 7 = halves rho .. rho + 7 of words 4d ..:
+                      // a funnel shift by 16 bits for odd rho, by 0 for even
+                      const uint32_t *w = hw0 + 4u * d, *v = hw1 + 4u * d;
+                      const uint32_t x0 = w[0], x1 = w[1], x2 = w[2], x3 = w[3], x4 = w[4];
+                      const uint32_t y0 = v[0], y1 = v[1], y2 = v[2], y3 = v[3], y4 = v[4];
+                      *reinterpret_cast<uint4 *>(win0 + d * 128u) =
+                          make_uint4(__funnelshift_r(x0, x1, sh), __funnelshift_r(x1, x2, sh),
+                                     __funnelshift_r(x2, x3, sh), __funnelshift_r(x3, x4, sh));
+                      *reinterpret_cast<uint4 *>(win1 + d * 128u) =
+                          make_uint4(__funnelshift_r(y0, y1, sh), __funnelshift_r(y1, y2, sh),
+                                     __funnelshift_r(y2, y3, sh), __funnelshift_r(y3, y4, sh));
                     }
                   }
                   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
