@@ -454,6 +454,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + S.tmem_slot);
   __shared__ int s_abort;
   __shared__ uint32_t s_abar[RPC];  // a~_i of the ciphertexts whose digits this CTA makes
+  __shared__ uint32_t s_gdone[kGBuf];  // warps done with each digit-phase staging buffer
 
   const uint32_t n = P.n, l = P.l, R = 2u * l;
   const uint32_t tid = threadIdx.x, warp = tid / 32u, lane = tid % 32u;
@@ -502,6 +503,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     s_abort = 0;
+    for (uint32_t b = 0; b < kGBuf; ++b) s_gdone[b] = 0u;
     for (uint32_t s = 0; s < kAStages; ++s) {
       mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], MC ? NP : 1u); mbar_init(&a_peer[s], 1);
     }
@@ -677,12 +679,25 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads, 1)
           }
         }
       }
-      __syncthreads();  // buffer `buf` is free again
-      if (tid == 0 && g + kGBuf < NGROUP && !s_abort) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&g_full[buf], 32768u);
-        bulk_g2s(smem + buf * 32768u, acc + (uint64_t)(row0 + (g + kGBuf) * G) * 2u * N, 32768u,
-                 &g_full[buf]);
+      // No CTA-wide barrier per group: each warp counts itself done with the
+      // buffer (acquire-release, so the count orders every warp's reads of
+      // it), and the last one refills it while the others go on.
+      __syncwarp();
+      if (lane == 0) {
+        uint32_t prev;
+        asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;"
+                     : "=r"(prev)
+                     : "r"(smem_u32(&s_gdone[buf]))
+                     : "memory");
+        if (prev == kThreads / 32u - 1u) {
+          s_gdone[buf] = 0u;
+          if (g + kGBuf < NGROUP && !s_abort) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&g_full[buf], 32768u);
+            bulk_g2s(smem + buf * 32768u, acc + (uint64_t)(row0 + (g + kGBuf) * G) * 2u * N, 32768u,
+                     &g_full[buf]);
+          }
+        }
       }
     }
     // This CTA multicasts exactly the digit rows it just wrote; the fence and
