@@ -213,14 +213,14 @@ def synth_pbs_per_image(T):
     return (8 * 12 * 12 + 128 + 10) * T
 
 
-def time_arm(fhe, keys, net, ct, B, variant, steps, warmup, streamed, world, local, flush):
+def time_arm(fhe, keys, net, ct, B, variant, steps, warmup, streamed, world, local, flush, graphs=True):
     """Warm-up, then `steps` timed steps of one variant of the network on
     device-resident inputs: CUDA events on the launching stream around each
     step (an L2-flushing write before each, outside the events), nvidia-smi
     clocks sampled during the timed region, the blind-rotation launches
     bracketed by their own events for the roofline."""
     import torch
-    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=not streamed, profile=True)
+    snn = fhe.Snn(keys, net, max_images=B, variant=variant, use_graph=graphs, profile=True)
     P = keys.params
     scores = [torch.empty((B, 10, P["n"] + 1), dtype=torch.int32, device="cuda") for _ in range(2)]
     stream = torch.cuda.current_stream()
@@ -345,7 +345,7 @@ def run_ours(args):
     arm = "tc" if variant == fhe.VARIANT_TC else "exact"
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     res = time_arm(fhe, keys, net, ct, B, variant, args.steps, args.warmup, streamed, world,
-                   local, flush)
+                   local, flush, graphs=not args.no_graphs)
     snn, per_image, total_ms = res["snn"], res["per_image"], res["total_ms"]
     value = job_rate(per_image * B * args.steps, world, total_ms)
 
@@ -389,7 +389,7 @@ def run_ours(args):
     exact = None
     if arm == "tc" and args.exact_steps > 0 and world == 1:
         xres = time_arm(fhe, keys, net, ct, B, fhe.VARIANT_EXACT, args.exact_steps,
-                        args.exact_warmup, streamed, world, local, flush)
+                        args.exact_warmup, streamed, world, local, flush, graphs=not args.no_graphs)
         xres["snn"].free()
         xvalue = per_image * B * args.exact_steps / (xres["total_ms"] / 1e3)
         exact = {"value": xvalue, "unit": UNIT, "steps": args.exact_steps,
@@ -417,7 +417,9 @@ def run_ours(args):
                    "schedule": ("streamed: each timed step starts one batch and, in the same "
                                 "bootstrap launches, finishes the batch before it (pipeline "
                                 "filled by the warm-up steps, drained after the timed region); "
-                                "one bootstrap launch per layer-skewed iteration")
+                                "one bootstrap launch per layer-skewed iteration, "
+                                + ("each iteration a replayed CUDA graph" if not args.no_graphs
+                                   else "launched directly"))
                                if streamed else
                                "one batch per step: layer-skewed, one bootstrap launch per "
                                "iteration, CUDA graph per iteration",
@@ -447,6 +449,9 @@ def main():
     # clusters
     ap.add_argument("--images", type=int, default=7)
     ap.add_argument("--variant", default="auto", choices=["auto", "exact", "tc"])
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every iteration's kernels directly instead of replaying "
+                         "one captured CUDA graph per iteration")
     ap.add_argument("--schedule", default="stream", choices=["stream", "batch"],
                     help="stream: batches pipelined across steps; batch: one batch per step")
     ap.add_argument("--e2e-steps", type=int, default=None,

@@ -380,9 +380,11 @@ typedef struct fhe_snn_desc {
   int32_t static_input;         /* 1: input reused every step (pixels)       */
   uint32_t max_images;          /* capacity: images per inference call       */
   int32_t variant;              /* FHE_VARIANT_* of the bootstraps           */
-  int32_t use_graph;            /* bit 0: capture each time step as a CUDA
-                                   graph; bit 1 (FHE_SNN_PROFILE): time the
-                                   blind rotations (fhe_snn_profile)        */
+  int32_t use_graph;            /* bit 0: run each time step as a captured
+                                   CUDA graph (fhe_snn_step, and the streamed
+                                   steps once every layer is active); bit 1
+                                   (FHE_SNN_PROFILE): time the blind
+                                   rotations (fhe_snn_profile)               */
   int32_t lif_mode;             /* FHE_LIF_MULTI_VALUE or FHE_LIF_TWO_PBS     */
 } fhe_snn_desc;
 
@@ -440,7 +442,16 @@ uint32_t fhe_snn_iterations(const fhe_snn *net);
  * batch completes.  fhe_snn_stream_flush runs the remaining steps so every
  * pushed batch completes, synchronizes `stream` when any destination is host
  * memory (returning the device status), and ends the stream.  While a stream
- * runs, fhe_snn_infer / fhe_snn_begin return FHE_EINVAL (and vice versa);
+ * runs, fhe_snn_infer / fhe_snn_begin return FHE_EINVAL (and vice versa).
+ * With use_graph bit 0 set, a step in which every layer is active (every
+ * step but the stream's first n_layers - 1 and those of the flush) launches
+ * exactly the work of the step T * slots later on the same buffers, slots =
+ * 1 + ceil((n_layers - 1) / T) being the batches in flight at once: each of
+ * those T * slots step kinds is captured as a CUDA graph on its first use
+ * and replayed after that (a new n_images or a change of the keys' tuning
+ * settings captures them again); the copy of a completed batch's scores to
+ * its caller stays outside the graph.  Graph memory is kept until
+ * fhe_snn_free;
  * fhe_snn_profile covers the launches since the stream's first push (with
  * profiling on, two events are kept per bootstrap launch of the stream:
  * meant for bounded measurement runs, not for unbounded serving).

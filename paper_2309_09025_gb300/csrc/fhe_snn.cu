@@ -13,7 +13,8 @@
 // t = tau - l in [0, T): all active layers' neurons (of all images) go through
 // ONE bootstrap launch per iteration, T + layers - 1 iterations in total,
 // instead of one mostly-empty launch per layer and step.  Each iteration is
-// captured once as a CUDA graph per batch size and replayed.
+// captured once as a CUDA graph per batch size and replayed; a stream of
+// batches replays one graph per kind of steady-state iteration.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -40,6 +41,18 @@ struct Layer {
   uint32_t *d_I;  // [max_images][out][n+1] (not used by a Poisson layer)
 };
 
+// One captured streamed iteration: its executable graph (and the graph it was
+// instantiated from, whose event-record nodes are re-pointed before every
+// replay), its kernel count, and per bracketed bootstrap launch the two
+// event-record nodes and the launch's ciphertext count.
+struct IterGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  std::vector<cudaGraphNode_t> ev_nodes;  // [launch][2]
+  std::vector<size_t> ev_counts;          // [launch]
+};
+
 // Streamed inference: batch b lives in slot b % nslots while its layers are
 // in flight (T + layers - 1 iterations); every iteration gathers the active
 // (layer, batch) segments into one contiguous bootstrap launch.
@@ -55,7 +68,23 @@ struct StreamState {
   std::vector<cudaEvent_t> ev;   // [launch][2]
   std::vector<size_t> ev_count;  // ciphertexts of each bracketed launch
   size_t ev_used = 0;
+  // Steady state (every layer active): iteration j launches the same work on
+  // the same buffers as iteration j + T * nslots, so with use_graph bit 0 one
+  // graph per residue j mod (T * nslots) is captured on first use and
+  // replayed; captured for batches of graph_ni images under the keys' tuning
+  // settings graph_tuning.
+  std::vector<IterGraph> graphs;
+  size_t graph_ni = 0;
+  std::vector<int64_t> graph_tuning;
 };
+
+static void drop_graphs(std::vector<IterGraph> &v) {
+  for (auto &g : v) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  v.clear();
+}
 }  // namespace
 
 struct fhe_snn {
@@ -81,6 +110,7 @@ struct fhe_snn {
   // captured graphs per batch size: one executable graph per iteration, its
   // kernel-node count and its bracketed bootstrap counts (two per iteration)
   struct GraphSet {
+    std::vector<int64_t> tuning;  // the keys' tuning settings at capture
     std::vector<cudaGraphExec_t> execs;
     std::vector<int64_t> kernels;
     std::vector<size_t> pbs_counts;
@@ -107,12 +137,21 @@ static uint32_t half_space(uint32_t log2_p) {
   return (1u << (log2_p - 1u)) * (1u << (31u - log2_p));
 }
 
+// The keys' settings that pick the launched blind-rotation kernels (variant
+// threshold, cluster shapes and their limits, forced options): a CUDA graph
+// captured under other values is captured again.
+static std::vector<int64_t> tuning_of(const fhe_keys *K) {
+  return {(int64_t)K->tc_min_batch, K->tc_cl8_tiles, K->tc_cl16_tiles, K->tc_split_ok,
+          K->tc_split_tiles, K->tc_force_cl, K->tc_force_mc, K->tc_l2_hints};
+}
+
 static uint32_t snn_iterations(const fhe_snn *S) {
   return S->desc.T + (uint32_t)S->layers.size() - 1u;
 }
 
 static void stream_release(StreamState *Z) {
   if (!Z) return;
+  drop_graphs(Z->graphs);
   for (auto *v : {&Z->spk, &Z->mem, &Z->I})
     for (auto &slot : *v)
       for (auto p : slot) cudaFree(p);
@@ -462,6 +501,7 @@ static int snn_iteration(fhe_snn *S, uint32_t tau, size_t ni, cudaStream_t st) {
 static int snn_capture(fhe_snn *S, size_t ni, cudaStream_t st) {
   const uint32_t iters = snn_iterations(S);
   fhe_snn::GraphSet set;
+  set.tuning = tuning_of(S->K);
   set.execs.assign(iters, (cudaGraphExec_t)0);
   set.kernels.assign(iters, 0);
   set.pbs_counts.assign(2u * iters, 0);
@@ -519,6 +559,14 @@ extern "C" int fhe_snn_step(fhe_snn *S, void *stream) {
   const size_t ni = S->cur_images;
   const uint32_t tau = S->next_iter;
   if (S->desc.use_graph & 1) {
+    auto old = S->graphs.find(ni);
+    if (old != S->graphs.end() && old->second.tuning != tuning_of(S->K)) {
+      // captured under other tuning settings: capture again (a graph still
+      // running is freed when it completes)
+      for (auto &g : old->second.execs)
+        if (g) cudaGraphExecDestroy(g);
+      S->graphs.erase(old);
+    }
     if (S->graphs.find(ni) == S->graphs.end()) {
       FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
       FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
@@ -622,6 +670,22 @@ static int stream_alloc(fhe_snn *S) {
   return FHE_OK;
 }
 
+// Make sure an event pair exists for the next bracketed launch (slot ev_used).
+static int stream_event_pair(StreamState &Z) {
+  if (2u * Z.ev_used + 2u <= Z.ev.size()) return FHE_OK;
+  cudaEvent_t a, b;
+  FHE_CUDA_TRY(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    (void)cudaGetLastError();
+    return FHE_ECUDA;
+  }
+  Z.ev.push_back(a);
+  Z.ev.push_back(b);
+  Z.ev_count.push_back(0);
+  return FHE_OK;
+}
+
 static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi, const fhe_lut *lut,
                             uint32_t *out, size_t stride, cudaStream_t st,
                             const uint64_t *seg_end = nullptr) {
@@ -629,14 +693,8 @@ static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi
   StreamState &Z = *S->stream;
   const uint32_t W = S->K->P.n + 1u;
   if (S->profile) {
-    if (2u * Z.ev_used + 2u > Z.ev.size()) {
-      cudaEvent_t a, b;
-      FHE_CUDA_TRY(cudaEventCreate(&a));
-      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); (void)cudaGetLastError(); return FHE_ECUDA; }
-      Z.ev.push_back(a);
-      Z.ev.push_back(b);
-      Z.ev_count.push_back(0);
-    }
+    const int rc = stream_event_pair(Z);
+    if (rc) return rc;
     S->K->prof_ev0 = Z.ev[2u * Z.ev_used];
     S->K->prof_ev1 = Z.ev[2u * Z.ev_used + 1u];
   }
@@ -651,8 +709,9 @@ static int stream_bootstrap(fhe_snn *S, const uint32_t *in, size_t lo, size_t hi
 
 // Iteration j of the stream: layer l runs batch b = (j - l) / T at time
 // t = (j - l) mod T for every pushed batch b (same recurrence as the
-// layer-skewed schedule of one inference).
-static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
+// layer-skewed schedule of one inference).  Everything but the copy of a
+// completed batch's scores to its caller (stream_deliver).
+static int stream_body(fhe_snn *S, uint64_t j, cudaStream_t st) {
   StreamState &Z = *S->stream;
   const fhe::Params &P = S->K->P;
   const uint32_t W = P.n + 1u, delta = P.delta();
@@ -733,17 +792,134 @@ static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
     if (S->layers[l].type != FHE_LAYER_POISSON)
       FHE_CUDA_TRY(cudaMemcpyAsync(Z.mem[slot[l]][l], pout_v + off[l] * W, bytes, cudaMemcpyDeviceToDevice, st));
   }
-  // 5. spike-count scores; a batch is complete after the last layer's step T-1
+  // 5. spike-count scores of the last layer
   const uint32_t lo = nl - 1u;
   if (on[lo]) {
     const uint32_t sl = slot[lo], t = tt[lo];
     rc = fhe::lwe_add(P.n, Z.spk[sl][lo], t ? Z.scores[sl] : NULL, 0u, ni * S->n_out, Z.scores[sl], st);
     if (rc) return rc;
-    if (t == T - 1u)
-      FHE_CUDA_TRY(cudaMemcpyAsync(Z.dst[sl], Z.scores[sl], sizeof(uint32_t) * ni * S->n_out * W,
-                                   Z.dst_host[sl] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
   }
   return FHE_OK;
+}
+
+// A batch is complete after the last layer's step T - 1: iteration j copies
+// its scores to the caller's buffer (host or device, given at staging).
+static int stream_deliver(fhe_snn *S, uint64_t j, cudaStream_t st) {
+  StreamState &Z = *S->stream;
+  const uint32_t T = S->desc.T, lo = (uint32_t)S->layers.size() - 1u;
+  if (j < lo || (j - lo) % T != T - 1u) return FHE_OK;
+  const uint64_t b = (j - lo) / T;
+  if (b >= Z.pushed) return FHE_OK;
+  const uint32_t sl = (uint32_t)(b % Z.nslots);
+  FHE_CUDA_TRY(cudaMemcpyAsync(Z.dst[sl], Z.scores[sl],
+                               sizeof(uint32_t) * Z.ni * S->n_out * (S->K->P.n + 1u),
+                               Z.dst_host[sl] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  return FHE_OK;
+}
+
+// Capture iteration j's body on the library stream into G.  The capture runs
+// nothing: the profiling event slots it took are handed back, and the graph's
+// event-record nodes that stand for them are located so that every replay
+// can point them at fresh events.
+static int stream_capture(fhe_snn *S, uint64_t j, IterGraph &G) {
+  StreamState &Z = *S->stream;
+  const size_t u0 = Z.ev_used;
+  // an iteration brackets two bootstrap launches at most: their event pairs
+  // are created before the capture starts
+  for (int k = 0; S->profile && k < 2; ++k, ++Z.ev_used) {
+    const int rc = stream_event_pair(Z);
+    if (rc) { Z.ev_used = u0; return rc; }
+  }
+  Z.ev_used = u0;
+  if (cudaStreamBeginCapture(S->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FHE_ECUDA;
+  }
+  const int64_t before = (int64_t)fhe::launches();
+  int rc = stream_body(S, j, S->gs);
+  G.kernels = (int64_t)fhe::launches() - before;
+  fhe::note_launches(-G.kernels);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(S->gs, &graph);
+  const size_t u1 = Z.ev_used;
+  Z.ev_used = u0;
+  if (rc || e != cudaSuccess) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    else (void)cudaGetLastError();
+    return rc ? rc : FHE_ECUDA;
+  }
+  G.ev_nodes.assign(2u * (u1 - u0), (cudaGraphNode_t)0);
+  G.ev_counts.assign(Z.ev_count.begin() + u0, Z.ev_count.begin() + u1);
+  if (u1 > u0) {
+    size_t nn = 0;
+    bool ok = cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    ok = ok && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess;
+    for (size_t q = 0; ok && q < nn; ++q) {
+      cudaGraphNodeType ty;
+      cudaEvent_t ev = nullptr;
+      ok = cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess;
+      if (!ok || ty != cudaGraphNodeTypeEventRecord) continue;
+      ok = cudaGraphEventRecordNodeGetEvent(nodes[q], &ev) == cudaSuccess;
+      for (size_t k = 0; ok && k < G.ev_nodes.size(); ++k)
+        if (Z.ev[2u * u0 + k] == ev) G.ev_nodes[k] = nodes[q];
+    }
+    for (auto nd : G.ev_nodes) ok = ok && nd != nullptr;
+    if (!ok) {
+      (void)cudaGetLastError();
+      cudaGraphDestroy(graph);
+      return FHE_ECUDA;
+    }
+  }
+  if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    G.exec = nullptr;
+    cudaGraphDestroy(graph);
+    return FHE_ECUDA;
+  }
+  G.graph = graph;
+  return FHE_OK;
+}
+
+// Run iteration j: its cached graph in the steady state when graphs are on,
+// else its launches directly; then the score delivery.
+static int stream_iteration(fhe_snn *S, uint64_t j, cudaStream_t st) {
+  StreamState &Z = *S->stream;
+  const uint32_t T = S->desc.T, nl = (uint32_t)S->layers.size();
+  const bool steady = (S->desc.use_graph & 1) && j + 1u >= nl && j < Z.pushed * T;
+  if (!steady) {
+    const int rc = stream_body(S, j, st);
+    return rc ? rc : stream_deliver(S, j, st);
+  }
+  const size_t period = (size_t)T * Z.nslots;
+  std::vector<int64_t> tuning = tuning_of(S->K);
+  if (Z.graph_ni != Z.ni || Z.graph_tuning != tuning || Z.graphs.size() != period) {
+    drop_graphs(Z.graphs);  // graphs still running are freed when they complete
+    Z.graphs.resize(period);
+    Z.graph_ni = Z.ni;
+    Z.graph_tuning.swap(tuning);
+  }
+  IterGraph &G = Z.graphs[j % period];
+  FHE_CUDA_TRY(cudaEventRecord(S->join_in, st));
+  FHE_CUDA_TRY(cudaStreamWaitEvent(S->gs, S->join_in, 0));
+  if (!G.exec) {
+    const int rc = stream_capture(S, j, G);
+    if (rc) { G = IterGraph(); return rc; }
+  }
+  // this replay's bootstrap launches are timed by the next free event pairs
+  for (size_t k = 0; S->profile && k < G.ev_counts.size(); ++k) {
+    const int rc = stream_event_pair(Z);
+    if (rc) return rc;
+    FHE_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_nodes[2u * k], Z.ev[2u * Z.ev_used]));
+    FHE_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev_nodes[2u * k + 1u],
+                                                      Z.ev[2u * Z.ev_used + 1u]));
+    Z.ev_count[Z.ev_used++] = G.ev_counts[k];
+  }
+  FHE_CUDA_TRY(cudaGraphLaunch(G.exec, S->gs));
+  fhe::note_launches(G.kernels);
+  FHE_CUDA_TRY(cudaEventRecord(S->join_out, S->gs));
+  FHE_CUDA_TRY(cudaStreamWaitEvent(st, S->join_out, 0));
+  return stream_deliver(S, j, st);
 }
 
 extern "C" int fhe_snn_stream_stage(fhe_snn *S, const uint32_t *ct_input, size_t ni, uint32_t *scores,

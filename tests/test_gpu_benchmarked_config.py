@@ -71,23 +71,26 @@ def test_p630_lif_thousand_bootstraps_match_oracle_hashes(fhe, variant):
 
 
 def test_streamed_csnn_t4_full_size_every_step(fhe, oracle_keys):
-    """The bench's network and schedule at full size on tensor cores: two
-    batches of 2 images pushed into one stream (the second batch's first
-    steps share bootstrap launches with the first batch's deeper layers),
-    all T = 4 steps of all three layers checked neuron by neuron on a sample,
+    """The bench's network and schedule at full size on tensor cores: three
+    batches of 2 images pushed into one stream (each batch's first steps
+    share bootstrap launches with the previous batch's deeper layers), all
+    T = 4 steps of all three layers checked neuron by neuron on a sample,
     through fhe_snn_stream_stage / fhe_snn_stream_iterate, the same
-    iteration code as fhe_snn_stream_push."""
+    iteration code as fhe_snn_stream_push.  As in the bench, the iterations
+    with every layer active run as CUDA graphs, one per residue of the step
+    mod 8: the third batch's iterations replay graphs captured during the
+    first two."""
     P, OK = oracle_keys("P630", 3)
     K = fhe.keygen_from_seed(P, 3)
     W = P["n"] + 1
     p = 1 << P["log2_p"]
-    T, B, NB = 4, 2, 2
+    T, B, NB = 4, 2, 3
     net = synth.csnn_net(T=T)
     sizes = [1152, 128, 10]
     nl = len(sizes)
     imgs = synth.stroke_images(5, B * NB).reshape(NB, B, -1)
     cts = [fhe.encrypt(K, imgs[b].reshape(-1), seed=11 + b).view(B, 28 * 28, W) for b in range(NB)]
-    snn = fhe.Snn(K, net, max_images=B, variant=fhe.VARIANT_TC, use_graph=False)
+    snn = fhe.Snn(K, net, max_images=B, variant=fhe.VARIANT_TC, use_graph=True)
     scores = [torch.empty((B, 10, W), dtype=torch.int32, device="cuda") for _ in range(NB)]
 
     def snap(batches):

@@ -144,3 +144,59 @@ def test_stream_rejects_mixed_sizes_and_infer_while_running(fhe):
     snn.stream_flush()
     snn.infer(x, 2, sc)  # usable again after the flush
     torch.cuda.synchronize()
+
+
+def test_stream_graph_replays_equal_direct_launches(fhe, oracle_keys):
+    """With graphs on, the steady-state iterations replay one captured graph
+    per residue j mod (T x slots); six batches at T = 2 replay every residue
+    at least once.  Scores, the profiled bootstrap launches and the kernel
+    count equal those of the same stream launched directly; a second stream
+    re-uses the graphs, a smaller batch size and a tuning change re-capture
+    them, and sampled images still equal the oracle."""
+    P, K = gpu_keys(fhe, "T0", 31)
+    _, OK = oracle_keys("T0", 31)
+    W = P["n"] + 1
+    net = small_net(11, 2)
+    variant = fhe.VARIANT_TC
+    try:
+        g_snn = fhe.Snn(K, net, max_images=2, variant=variant, use_graph=True, profile=True)
+    except fhe.FheError as e:
+        if e.code != fhe.FHE_EUNSUPPORTED:
+            raise
+        variant = fhe.VARIANT_EXACT
+        g_snn = fhe.Snn(K, net, max_images=2, variant=variant, use_graph=True, profile=True)
+    d_snn = fhe.Snn(K, net, max_images=2, variant=variant, use_graph=False, profile=True)
+    batches = []
+    for b in range(6):
+        x = synth.bernoulli_spikes(80 + b, 2, 2 * 6, 0.5).reshape(2, 2, 6)
+        batches.append(O.encrypt(P, OK, x.reshape(-1), 900 + b).reshape(2, 2, 6, W))
+
+    def run(snn, bs, n_images=2):
+        k0 = fhe.kernel_launches()
+        out = run_stream(fhe, snn, [b[:, :n_images] for b in bs], W, 3, host=False, n_images=n_images)
+        return out, fhe.kernel_launches() - k0, snn.profile()
+
+    got, kg, pg = run(g_snn, batches)
+    ref, kd, pd = run(d_snn, batches)
+    for b in range(6):
+        assert np.array_equal(got[b], ref[b]), f"batch {b}"
+    assert kg == kd
+    assert pg[1:] == pd[1:] and pg[1] == 2 * 6 + 3 - 1  # one bootstrap launch per iteration
+    for b, i in ((0, 0), (5, 1)):
+        want = O.snn_encrypted(P, OK, net, batches[b][:, i], nthreads=NTHREADS)["scores"]
+        assert np.array_equal(got[b][i], want), f"oracle: batch {b} image {i}"
+    again, _, _ = run(g_snn, batches[:3])  # cached graphs of the first stream
+    for b in range(3):
+        assert np.array_equal(again[b], ref[b])
+    one, _, _ = run(g_snn, batches[:4], n_images=1)  # other batch size
+    for b in range(4):
+        assert np.array_equal(one[b][0], ref[b][0])
+    if variant == fhe.VARIANT_TC:
+        K.set_tc_option(fhe.TC_OPT_CLUSTER, 8)
+        try:
+            moved, _, _ = run(g_snn, batches[:4])
+        finally:
+            K.set_tc_option(fhe.TC_OPT_CLUSTER, 0)
+        for b in range(4):
+            assert np.array_equal(moved[b], ref[b])
+    assert K.status() == fhe.FHE_OK
