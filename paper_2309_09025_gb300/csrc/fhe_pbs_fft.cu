@@ -36,25 +36,64 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
   return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// In-place radix-2 FFT of `cnt` arrays of M points in shared memory whose
-// inputs were stored at bit-reversed positions.  tw[m] = exp(+2 pi i m / M)
-// for m < M/2; `inverse` uses the conjugate twiddles (negative exponent).
-template <int M>
-__device__ void fft_stages(double2 *a, int cnt, const double2 *__restrict__ tw, bool inverse) {
-  for (int len = 2; len <= M; len <<= 1) {
-    const int half = len >> 1, stride = M / len;
-    for (int t = threadIdx.x; t < cnt * (M / 2); t += kFftThreads) {
-      const int arr = t / (M / 2), bt = t % (M / 2);
-      const int g = bt / half, pos = bt % half;
-      double2 *x = a + (size_t)arr * M;
-      const int i1 = g * len + pos, i2 = i1 + half;
-      const double2 w = __ldg(tw + pos * stride);
-      const double2 y = inverse ? cmulc(x[i2], w) : cmul(x[i2], w);
-      const double2 u = x[i1];
-      x[i1] = make_double2(u.x + y.x, u.y + y.y);
-      x[i2] = make_double2(u.x - y.x, u.y - y.y);
+// In-place FFT of `cnt` arrays of M points in shared memory whose inputs
+// were stored at bit-reversed positions (decimation in time).  With
+// bit-reversed input, the four consecutive blocks B0..B3 of q points in a
+// group of 4q hold the q-point transforms D_r of the subsequences x[4m + r]
+// in the order D_0, D_2, D_1, D_3; one radix-4 pass merges them:
+//   a_r = W^{rp} D_r[p]  (W = exp(+-2 pi i / 4q), p < q),
+//   Z[p + kq] = sum_r a_r (+-i)^{rk},  k = 0..3,
+// three twiddle products per four points where two radix-2 passes take four
+// (none in the first pass, q = 1).  An odd log2 M starts with one radix-2
+// pass of unit twiddles.  tw[m] = exp(+2 pi i m / M) for m < 3M/4;
+// `inverse` uses the conjugate twiddles (negative exponent).
+template <int M, int Q>
+__device__ __forceinline__ void fft_radix4_passes(double2 *a, int cnt, const double2 *__restrict__ tw,
+                                                  bool inverse) {
+  if constexpr (Q < M) {
+    constexpr int stride = M / (4 * Q);  // W^{rp} = tw[r p stride]
+    for (int t = threadIdx.x; t < cnt * (M / 4); t += kFftThreads) {
+      const int arr = t / (M / 4), bt = t % (M / 4);
+      const int g = bt / Q, p = bt % Q;
+      double2 *x = a + (size_t)arr * M + 4 * Q * g + p;
+      double2 a0 = x[0], a1 = x[2 * Q], a2 = x[Q], a3 = x[3 * Q];
+      if constexpr (Q > 1) {
+        const double2 w1 = __ldg(tw + p * stride), w2 = __ldg(tw + 2 * p * stride),
+                      w3 = __ldg(tw + 3 * p * stride);
+        a1 = inverse ? cmulc(a1, w1) : cmul(a1, w1);
+        a2 = inverse ? cmulc(a2, w2) : cmul(a2, w2);
+        a3 = inverse ? cmulc(a3, w3) : cmul(a3, w3);
+      }
+      const double2 s02 = make_double2(a0.x + a2.x, a0.y + a2.y);
+      const double2 d02 = make_double2(a0.x - a2.x, a0.y - a2.y);
+      const double2 s13 = make_double2(a1.x + a3.x, a1.y + a3.y);
+      // j13 = +i (a1 - a3) forward, -i (a1 - a3) inverse
+      const double2 d13 = make_double2(a1.x - a3.x, a1.y - a3.y);
+      const double2 j13 = inverse ? make_double2(d13.y, -d13.x) : make_double2(-d13.y, d13.x);
+      x[0] = make_double2(s02.x + s13.x, s02.y + s13.y);
+      x[Q] = make_double2(d02.x + j13.x, d02.y + j13.y);
+      x[2 * Q] = make_double2(s02.x - s13.x, s02.y - s13.y);
+      x[3 * Q] = make_double2(d02.x - j13.x, d02.y - j13.y);
     }
     __syncthreads();
+    fft_radix4_passes<M, 4 * Q>(a, cnt, tw, inverse);
+  }
+}
+
+template <int M>
+__device__ void fft_stages(double2 *a, int cnt, const double2 *__restrict__ tw, bool inverse) {
+  constexpr int LOGM = (M == 512) ? 9 : 10;
+  if constexpr ((LOGM & 1) != 0) {
+    for (int t = threadIdx.x; t < cnt * (M / 2); t += kFftThreads) {
+      double2 *x = a + 2 * t;  // arrays are contiguous: pair t of all of them
+      const double2 u = x[0], v = x[1];
+      x[0] = make_double2(u.x + v.x, u.y + v.y);
+      x[1] = make_double2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+    fft_radix4_passes<M, 2>(a, cnt, tw, inverse);
+  } else {
+    fft_radix4_passes<M, 1>(a, cnt, tw, inverse);
   }
 }
 
@@ -81,8 +120,11 @@ __global__ void __launch_bounds__(kFftThreads)
   for (int k = threadIdx.x; k < M; k += kFftThreads) out[(size_t)blockIdx.x * M + k] = sh[k];
 }
 
+// Shared memory holds 4 CTAs per SM at N = 1024 (P630: 56 KB each) and 2 at
+// N = 2048 (80 KB); the bound of 4 CTAs keeps registers from lowering the
+// first (0: no bound for the second, which needs no more than 128).
 template <int N>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, N == 1024 ? 4 : 0)
     k_blind_rotate_fft(Params P, const double2 *__restrict__ kspec, const double2 *__restrict__ twist,
                        const double2 *__restrict__ tw, const uint32_t *__restrict__ ct_in,
                        size_t count, const __grid_constant__ LutArgs lut,
@@ -228,20 +270,20 @@ int fft_prepare(fhe_keys *K) {
   const Params &P = K->P;
   if (K->d_fft_kspec) return FHE_OK;
   const uint32_t M = P.N / 2u;
-  std::vector<double2> twist(M), tw(M / 2u);
+  std::vector<double2> twist(M), tw(3u * M / 4u);
   const double pi = 3.14159265358979323846264338327950288;
   for (uint32_t k = 0; k < M; ++k)
     twist[k] = make_double2(cos(pi * (double)k / (double)P.N), sin(pi * (double)k / (double)P.N));
-  for (uint32_t m = 0; m < M / 2u; ++m)
+  for (uint32_t m = 0; m < 3u * M / 4u; ++m)
     tw[m] = make_double2(cos(2.0 * pi * (double)m / (double)M), sin(2.0 * pi * (double)m / (double)M));
   const size_t polys = (size_t)P.n * P.rows() * 2u;
   if (cudaMalloc(&K->d_fft_twist, sizeof(double2) * M) != cudaSuccess ||
-      cudaMalloc(&K->d_fft_tw, sizeof(double2) * (M / 2u)) != cudaSuccess ||
+      cudaMalloc(&K->d_fft_tw, sizeof(double2) * (3u * M / 4u)) != cudaSuccess ||
       cudaMalloc(&K->d_fft_kspec, sizeof(double2) * M * polys) != cudaSuccess ||
       cudaMalloc(&K->d_fft_maxerr, sizeof(unsigned long long)) != cudaSuccess)
     return FHE_ENOMEM;
   FHE_CUDA_TRY(cudaMemcpy(K->d_fft_twist, twist.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
-  FHE_CUDA_TRY(cudaMemcpy(K->d_fft_tw, tw.data(), sizeof(double2) * (M / 2u), cudaMemcpyHostToDevice));
+  FHE_CUDA_TRY(cudaMemcpy(K->d_fft_tw, tw.data(), sizeof(double2) * (3u * M / 4u), cudaMemcpyHostToDevice));
   FHE_CUDA_TRY(cudaMemset(K->d_fft_maxerr, 0, sizeof(unsigned long long)));
   if (M == 512u)
     k_key_spectra<512><<<(unsigned)polys, kFftThreads, 512 * 16>>>(
