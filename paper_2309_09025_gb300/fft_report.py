@@ -15,8 +15,9 @@ parameter set), and the fraction of FFT outputs bit-identical to the exact
 ones.  It also measures the device's FP64 peak (cuBLAS DGEMM through torch,
 best of several 4096^3 products) and reports the FFT blind rotation's FP64
 rate against it: per CMux step, (k+1) l forward and k+1 inverse complex
-transforms of M = N/2 points at 5 M log2 M flops each (the radix-2 count) plus
-(k+1)^2 l M complex multiply-adds of 8 flops.
+transforms of M = N/2 points at 5 M log2 M flops each (the conventional
+radix-2 count; the kernel's radix-4 passes execute fewer) plus (k+1)^2 l M
+complex multiply-adds of 8 flops.
 """
 import argparse
 import json
