@@ -69,3 +69,35 @@ def test_traffic_record_is_used_only_for_the_captured_kernel_source(tmp_path, mo
     src.write_text("kernel v2\n")
     value, why = bench.recorded_traffic("tc", 9030.0)
     assert value is None and "changed" in why
+
+
+def _run_bench(args, **env):
+    import json
+    import subprocess
+    e = dict(os.environ)
+    e.update({k: str(v) for k, v in env.items()})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=e,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+
+
+def test_reference_arm_prints_one_oracle_line_on_rank_zero_only():
+    """bench.py --impl reference times the oracle on the host cores and
+    prints one line of the bench contract (its cpu_baseline and e2e describe
+    this run); under torchrun the other ranks exit 0 without work."""
+    import bench
+    lines = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert (d["steps"], d["warmup"]) == (1, 0)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    from paper_2309_09025_gb300 import synth
+    assert d["config"]["workload"] == bench.workload_name(dict(synth.P630), 4, 7)
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                      RANK=1, WORLD_SIZE=2, LOCAL_RANK=1) == []
